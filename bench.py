@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the mechanics step (binning + neighbour-gather velocity + AB2).
+
+Default workload: the 20M-cell clustered population (16M cells in a 2.5 mm
+core + 4M uniform in a 10 mm cube, voxel 30 um), the configuration whose
+memory roofline the project is measured against.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--mode kahan|mixed|fp64] [--scale S]
+
+One step = one pass of the whole hot path (bin, force, AB2) over all cells.
+`value` is device-timed (CUDA events on the library's stream, state resident
+in HBM); `e2e` goes through the C ABI with the positions copied in from pinned
+host memory and read back every step.  Under torchrun every rank advances its
+own copy of the workload on its own GPU (independent replicas; the method
+needs no exchange between GPUs), and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mechanics cell-steps/s (bin+force+AB2), batched vs plain, at <=1e-3 um pos error"
+UNIT = "cell-steps/s"
+# Algorithmic bytes (compulsory HBM traffic) of the fixed byte model.
+FORCE_BYTES_PER_CELL = 84      # read x 24 + params 12 + v_prev 12, write x 24 + v 12
+STEP_BYTES_PER_CELL = 228      # key+hist 28, scatter 116, force+AB2 84
+STEP_BYTES_PER_VOXEL = 20      # histogram zero/atomics 12, scan 8
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_traffic.json")
+FORCE_SRC = os.path.join(ROOT, "paper_2306_11544_gb300", "csrc", "mech_force.cu")
+DTYPES = {"kahan": "f32 (positions f32 + Kahan c)", "mixed": "f32 (positions f64)", "fp64": "f64"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="clustered_20m")
+    p.add_argument("--scale", type=float, default=1.0)
+    p.add_argument("--mode", default="kahan", choices=["kahan", "mixed", "fp64"])
+    p.add_argument("--voxel", type=float, default=0.0, help="internal voxel side (0: the workload's)")
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--graph", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def force_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, or None if
+    the kernel source changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        with open(FORCE_SRC, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if t.get("source_sha256_16") != h:
+            return None
+        return t
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.index = index
+        self.enabled = enabled
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                     "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self._t = threading.Thread(target=self._read, daemon=True)
+                self._t.start()
+                time.sleep(0.3)
+            except FileNotFoundError:
+                self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"], "samples": 0}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name, scale):
+    from paper_2306_11544_gb300 import synth
+    fn = synth.WORKLOADS[name]
+    return fn(seed=0, scale=scale)
+
+
+def describe(pop_or_ens, name, args, n, V):
+    from paper_2306_11544_gb300 import synth
+    cfg = {"workload": name, "cells": n, "voxels": V, "mode": args.mode, "scale": args.scale}
+    if isinstance(pop_or_ens, synth.Population):
+        p = pop_or_ens
+        cfg.update({"voxel_um": p.h if not args.voxel else args.voxel, "dt_min": p.dt, "A": p.A,
+                    "domain_um": [float(p.lo[0]), float(p.hi[0])]})
+        if name == "clustered_20m":
+            cfg["layout"] = "16M cells uniform in a 2.5 mm ball + 4M uniform in a 10 mm cube, R 8.41 um"
+    else:
+        cfg.update({"replicates": len(pop_or_ens.reps)})
+    cfg["l2"] = "no flush: per-step working set (state + voxel arrays) is > 20x the 129 MB L2"
+    return cfg
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on a bounded sample
+    (the same workload recipe at a reduced cell count), timed on host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2306_11544_gb300 import synth
+    oracle.build()
+    scale = args.scale * (1.0 / 16.0 if args.workload == "clustered_20m" else 0.05)
+    pop = make_workload(args.workload, scale)
+    reps = [pop] if isinstance(pop, synth.Population) else pop.reps
+    states = []
+    for p in reps:
+        states.append([p, p.xyz.copy(), np.zeros_like(p.xyz), oracle.grid_dims(p.lo, p.hi, p.h)])
+    n = sum(p.n for p in reps)
+
+    def one_step():
+        for st in states:
+            p, x, vp, dims = st
+            st[1], st[2], _ = oracle.run(x, p.R, p.ccr, p.cca, p.A, p.lo, p.h, dims, p.dt, 1, vprev=vp)
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    t = time.perf_counter() - t0
+    value = n * args.steps / t
+    sample = f"{args.workload} recipe at scale {scale:g} ({n} cells, same densities); one oracle step per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": n, "mode": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(pop):
+    """The oracle on the host cores: one full step of the same workload."""
+    import oracle
+    from paper_2306_11544_gb300 import synth
+    oracle.build()
+    reps = [pop] if isinstance(pop, synth.Population) else pop.reps
+    n = sum(p.n for p in reps)
+    t0 = time.perf_counter()
+    for p in reps:
+        oracle.run(p.xyz, p.R, p.ccr, p.cca, p.A, p.lo, p.h, oracle.grid_dims(p.lo, p.hi, p.h), p.dt, 1)
+    t = time.perf_counter() - t0
+    return {"value": n / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one full oracle step (bin+force+AB2, FP64) of all {n} cells, {t:.1f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+    from paper_2306_11544_gb300 import build as libbuild
+    from paper_2306_11544_gb300 import mech, synth
+
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    if rank == 0:
+        libbuild.build()
+    if pg:
+        pg.barrier()
+    mech.load_library()
+
+    wl = make_workload(args.workload, args.scale)
+    if isinstance(wl, synth.Population):
+        m = mech.Mech.from_population(wl, mode=args.mode)
+        n = wl.n
+    else:
+        m = mech.Mech.from_ensemble(wl, mode=args.mode)
+        n = wl.n_total
+    if args.voxel:
+        m.set_internal_voxel(args.voxel)
+    if args.block:
+        m.set_launch(args.block)
+    stream = torch.cuda.Stream()
+    m.set_stream(stream)
+    if args.graph:
+        m.set_graph(args.graph)
+    info = m.info()
+    V = info["n_voxels"]
+
+    # warm-up (also builds the first binning)
+    m.step(args.warmup)
+    m.sync()
+
+    # timed region: K steps, events on the library's stream, phase events inside
+    profile = not args.graph
+    if profile:
+        m.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local, enabled=not args.no_clocks) as clocks:
+        ev0.record(stream)
+        m.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    m.sync()
+    ms = ev0.elapsed_time(ev1)
+    phases, psteps = m.read_profile() if profile else ({}, 0)
+    if profile:
+        m.set_profiling(False)
+    t_max = ms
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+        pg.barrier()
+    total_cells = n * ws
+    value = total_cells * args.steps / (t_max * 1e-3)
+
+    # end to end through the C ABI: pinned host positions in, step, positions out
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        m.positions(out=xh)
+        for _ in range(2):
+            m.write_positions(xh)
+            m.step(1)
+            m.positions(out=xh)
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            m.write_positions(xh)
+            m.step(1)
+            m.positions(out=xh)
+        te = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([te], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": total_cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
+               "d2h_bytes_per_step": 24 * n, "steps": args.e2e_steps,
+               "path": "mech_write_positions (pinned host) -> mech_step(1) -> mech_read_positions (pinned host)"}
+    m.close()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    peak, peak_kind = hbm_peak()
+    roof = None
+    if profile and psteps:
+        t_force = phases["force"] / psteps * 1e-3
+        ach = FORCE_BYTES_PER_CELL * n / t_force / 1e9
+        tr = force_traffic()
+        roof = {"bound": "hbm", "kernel": "k_force_mixed" if args.mode != "fp64" else "k_force_fp64",
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "bytes_per_launch": FORCE_BYTES_PER_CELL * n,
+                "bytes_model": f"{FORCE_BYTES_PER_CELL} B/cell (x, params, v_prev in; x, v out)",
+                "launch_ms": 1e3 * t_force,
+                "traffic": None if tr is None else tr.get("dram_bytes_per_cell", 0) * n,
+                "traffic_source": None if tr is None else tr.get("source")}
+    step_bytes = STEP_BYTES_PER_CELL * n + STEP_BYTES_PER_VOXEL * V
+    step_s = t_max * 1e-3 / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.mode], "data": "synthetic",
+        "config": describe(wl, args.workload, args, n, V),
+        "roofline": roof,
+        "step_roofline": {"bytes_per_step": step_bytes, "model": "228 B/cell + 20 B/voxel",
+                          "achieved": step_bytes / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": step_bytes / step_s / 1e9 / peak},
+        "phases_ms_per_step": {k: v / psteps for k, v in phases.items()} if psteps else None,
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": info["launches_per_step"] * args.steps,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * mech.h -- C ABI of libmech, a GB300 (sm_103a) implementation of the
+ * per-time-step cell-mechanics update of an agent-based multicellular
+ * simulation: the "update velocity" region that the paper analyses in
+ * Sec. 5.4 (a loop over all cells that updates each cell's velocity from its
+ * neighbouring cells, found through the mechanics voxel grid; Listing 4 and
+ * the non-empty-voxel variant that follows it), plus the position update.
+ *
+ * One step (mech_step) does, for every cell i:
+ *   1. Binning.  i_d = clamp(floor((x_d - lo_d) / h), 0, n_d - 1) on a uniform
+ *      voxel grid of side h over the domain [lo, hi] (n_d = ceil((hi_d -
+ *      lo_d) / h)); cells outside the domain are counted in the edge voxel;
+ *      the cells are then permuted into voxel order by a counting sort
+ *      (histogram, exclusive scan, scatter) whose order inside a voxel is
+ *      ascending caller index.  This is the GPU form of the paper's lesson
+ *      that cells should be stored and computed in the order of the 3-D mesh
+ *      and that empty voxels should cost nothing (Sec. 5.4).
+ *   2. Velocity.  Over every cell j != i in the 27 voxels around i's voxel,
+ *      with d = |x_i - x_j| > 0 and S = R_i + R_j:
+ *        c_r = sqrt(ccr_i ccr_j) (1 - d/S)^2          if d < S,   else 0
+ *        c_a = sqrt(cca_i cca_j) (1 - d/(A S))^2      if d < A S, else 0
+ *        v_i = sum_j (c_r - c_a) (x_i - x_j) / d.
+ *   3. Two-step Adams-Bashforth: x_i += dt (1.5 v_i - 0.5 v_i,prev), then
+ *      v_i,prev = v_i.  Before the first step v_prev = 0.
+ * The paper names these regions but prints none of the formulas; the force
+ * law and the integrator above are the problem this library solves.
+ *
+ * Units: um and min.  All per-cell arrays are in the CALLER's cell order
+ * (index 0..n-1, concatenated over replicates for a batch); positions and
+ * velocities are interleaved xyz, 3*n doubles.  The library copies every
+ * input array before returning; the caller owns every output buffer.  The
+ * internal voxel order is never exposed.
+ *
+ * Every call returns MECH_OK (0) or a negative MECH_E_* code; the message of
+ * the last failure on the calling thread is in mech_last_error().  Calls on
+ * one handle are not thread-safe; distinct handles are independent.
+ * Device work is queued on the handle's CUDA stream (mech_set_stream); the
+ * read calls synchronise that stream.  Host pointers may be pageable or
+ * pinned; pinned buffers copy faster.
+ */
+#ifndef MECH_H
+#define MECH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MECH_API __attribute__((visibility("default")))
+#else
+#define MECH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MECH_OK 0
+#define MECH_E_ARG (-1)              /* invalid argument (null pointer, bad size, bad mode) */
+#define MECH_E_NONFINITE (-2)        /* NaN or Inf in an input array or parameter */
+#define MECH_E_VOXEL_TOO_SMALL (-3)  /* voxel_size < 2 A max R: the 27-voxel stencil would miss pairs */
+#define MECH_E_OOM (-4)              /* device allocation failed, or the grid does not fit */
+#define MECH_E_CUDA (-5)             /* a CUDA runtime call failed */
+#define MECH_E_TIMEOUT (-6)          /* a bounded device wait gave up */
+#define MECH_E_DEVICE_FLAG (-7)      /* a kernel raised its error flag (non-finite state, bad index) */
+#define MECH_E_STATE (-8)            /* call out of order (e.g. mech_step before mech_set_params) */
+
+/* Precision modes (mech_set_precision). */
+#define MECH_FP64 0           /* positions, velocities and pair arithmetic in FP64 */
+#define MECH_MIXED_FP64POS 1  /* pair arithmetic and sums in FP32, positions and AB2 accumulation in FP64 */
+#define MECH_MIXED_KAHAN 2    /* pair arithmetic in FP32, positions in FP32 with a Kahan compensation term */
+
+typedef struct mech mech_t;
+
+/* Message of the last failing call on this thread ("" if none). */
+MECH_API const char* mech_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+MECH_API int mech_version(void);
+
+/*
+ * Create a handle for one population of n >= 0 cells on the current CUDA
+ * device.  xyz: 3n doubles; R (radius, > 0), ccr, cca (>= 0): n doubles each;
+ * type: n int32 (carried, unused by the force; may be NULL).  The arrays are
+ * copied.  Precision defaults to MECH_MIXED_FP64POS; parameters must be set
+ * with mech_set_params before the first step.  The domain defaults to a cube
+ * centred at the origin whose half side is 1.5 times the largest |coordinate|
+ * (at least half a voxel).  *h is set to NULL on failure.
+ */
+MECH_API int mech_create(mech_t** h, int64_t n, const double* xyz, const double* R, const double* ccr,
+                const double* cca, const int32_t* type);
+
+/*
+ * Create a handle for n_rep >= 1 independent replicates (counts[r] >= 0 cells
+ * each) advanced together: every kernel launch covers all replicates, each on
+ * its own voxel grid.  The per-cell arrays hold the replicates one after
+ * another (replicate 0 first), sum(counts) cells in total.
+ */
+MECH_API int mech_create_batch(mech_t** h, int32_t n_rep, const int64_t* counts, const double* xyz,
+                      const double* R, const double* ccr, const double* cca, const int32_t* type);
+
+/*
+ * A >= 1: adhesion range factor; voxel_size: mechanics voxel side (um), must
+ * be >= 2 A max_i R_i (else MECH_E_VOXEL_TOO_SMALL); dt > 0: time step (min).
+ * Applies to every replicate.  Resets nothing else.
+ */
+MECH_API int mech_set_params(mech_t* h, double A, double voxel_size, double dt);
+
+/*
+ * Domain of replicate rep (rep = -1: every replicate): lo[3] < hi[3].  The
+ * grid has n_d = ceil((hi_d - lo_d) / voxel) voxels per axis; cells outside
+ * it stay where they are and are binned into the edge voxel (there are no
+ * walls).  Fails with MECH_E_OOM if the grids of all replicates exceed
+ * 2^31 voxels or device memory.
+ */
+MECH_API int mech_set_domain(mech_t* h, int32_t rep, const double lo[3], const double hi[3]);
+
+/* MECH_FP64, MECH_MIXED_FP64POS or MECH_MIXED_KAHAN.  Converts the current
+ * state (positions and previous velocities) to the new representation. */
+MECH_API int mech_set_precision(mech_t* h, int mode);
+
+/*
+ * Voxel side used internally for binning (the autotuner's knob).  0 restores
+ * voxel_size.  Must be >= 2 A max R (1 + 1e-6).  The set of interacting pairs
+ * does not depend on it; the FP32 summation order does.
+ */
+MECH_API int mech_set_internal_voxel(mech_t* h, double voxel);
+
+/* Kernel shape: threads per block of the force kernel (32..256, multiple of
+ * 32; 0 = default).  Autotuner knob; results do not depend on it. */
+MECH_API int mech_set_launch(mech_t* h, int32_t force_block);
+
+/* Stream (a cudaStream_t) for all device work of this handle; NULL = the
+ * handle's own stream.  The caller keeps the stream alive. */
+MECH_API int mech_set_stream(mech_t* h, void* stream);
+
+/*
+ * Use a CUDA graph holding `steps_per_graph` consecutive steps (an even
+ * number >= 2; 0 disables graphs).  mech_step then replays the graph and
+ * launches the remainder directly.  The graph is (re)captured on first use
+ * after any change of parameters, domain, precision or launch shape; capture
+ * happens on the handle's stream.
+ */
+MECH_API int mech_set_graph(mech_t* h, int32_t steps_per_graph);
+
+/* Advance n_steps >= 0 steps.  Asynchronous on the handle's stream. */
+MECH_API int mech_step(mech_t* h, int64_t n_steps);
+
+/* Velocities v_n of the current positions (steps 1-2 only, no integration);
+ * writes 3n doubles in caller order.  Synchronous. */
+MECH_API int mech_compute_velocities(mech_t* h, double* out3n);
+
+/*
+ * Per-phase timing with CUDA events on the handle's stream: while enabled,
+ * every directly launched step (graphs are bypassed) records events around
+ * its phases.  mech_read_profile waits for the stream and returns the summed
+ * device milliseconds of each phase since the previous read: phase_ms[0] scan
+ * (histogram prefix sum), [1] scatter, [2] in-voxel ordering and FP32 record
+ * build, [3] velocity + AB2 (+ next-step histogram), and the number of steps
+ * recorded (at most 4096 between reads).
+ */
+MECH_API int mech_set_profiling(mech_t* h, int32_t enable);
+MECH_API int mech_read_profile(mech_t* h, double* phase_ms, int64_t* steps);
+
+/* Wait for the handle's stream; report a raised device error flag as
+ * MECH_E_DEVICE_FLAG. */
+MECH_API int mech_sync(mech_t* h);
+
+/* Current positions (3n doubles, caller order).  In MECH_MIXED_KAHAN mode the
+ * value is x_hi - c evaluated in FP64.  Synchronous. */
+MECH_API int mech_read_positions(mech_t* h, double* out3n);
+
+/* Velocities of the last step (v_n, computed from the positions at the start
+ * of that step), 3n doubles in caller order; zeros before the first step. */
+MECH_API int mech_read_velocities(mech_t* h, double* out3n);
+
+/* Replace all positions (3n doubles, caller order); previous velocities are
+ * kept.  Asynchronous: the host buffer must stay valid until the next
+ * synchronising call on the handle. */
+MECH_API int mech_write_positions(mech_t* h, const double* xyz3n);
+
+/*
+ * Exact state for checkpoint/resume: xyz (3n; in MECH_MIXED_KAHAN mode the
+ * FP32 x_hi values), vprev (3n), comp (3n, the Kahan compensation c, zeros in
+ * the other modes; may be NULL), step (may be NULL).  mech_load_state takes
+ * the same arrays; a run resumed from a saved state is bitwise identical to
+ * the uninterrupted run with the same precision, parameters and internal voxel.
+ */
+MECH_API int mech_read_state(mech_t* h, double* xyz, double* vprev, double* comp, int64_t* step);
+MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const double* comp, int64_t step);
+
+/*
+ * Binning of the current positions, for inspection (steps 1 of the update,
+ * without advancing): key (n, caller order), count (V), start (V + 1) and
+ * order (n: caller index of the cell at each sorted position), V = total
+ * voxels of all replicates (mech_info).  Any output may be NULL.  Synchronous.
+ */
+MECH_API int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order);
+
+typedef struct {
+    int64_t n_cells;
+    int32_t n_rep;
+    int32_t mode;
+    int64_t n_voxels;     /* total voxels of all replicate grids */
+    int32_t dims[3];      /* grid of replicate 0 */
+    double voxel;         /* internal voxel side */
+    int64_t step;         /* steps taken */
+    int32_t launches_per_step; /* kernel launches of one steady-state step */
+    int32_t graph_steps;
+    int64_t device_bytes; /* device memory held by the handle */
+} mech_info_t;
+
+MECH_API int mech_info(mech_t* h, mech_info_t* out);
+
+/* Grid of replicate rep: lo[3], dims[3], voxel offset in the global index. */
+MECH_API int mech_grid(mech_t* h, int32_t rep, double* lo3, int32_t* dims3, int64_t* voxel_base);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+MECH_API int mech_destroy(mech_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MECH_H */

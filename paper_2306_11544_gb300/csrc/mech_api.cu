@@ -1,0 +1,836 @@
+// C ABI of libmech (declared in include/mech.h): handle lifetime, device
+// buffers, voxel grids, the per-step launch sequence, CUDA-graph replay and the
+// caller-order read/write/checkpoint calls.  No allocation happens inside
+// mech_step: every buffer is sized when the handle, its domain or its voxel
+// side is set (the GPU form of the paper's first lesson, Sec. 4.3: no memory
+// management inside the hot loop).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mech.h"
+#include "mech_internal.cuh"
+
+using namespace mk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess) return fail(MECH_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define MECH_TRY(expr)             \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != MECH_OK) return rc_; \
+    } while (0)
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+struct mech {
+    int dev = 0;
+    int sms = 152;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int mode = kMixedFP64Pos;
+    int64_t n = 0;
+    int32_t nrep = 0;
+    uint32_t npad = 0;
+    std::vector<int64_t> counts, cbase;
+    std::vector<std::array<double, 3>> dom_lo, dom_hi;
+    std::vector<bool> dom_auto;
+    std::vector<double> maxabs;  // per replicate, for the default domain
+    double maxR = 0.0;
+    double A = 0.0, voxel_user = 0.0, voxel_int = 0.0, dt = 0.0;
+    bool params_set = false;
+    bool grid_dirty = true;
+    // grids
+    std::vector<GridDev> grids;
+    uint32_t V = 0, Vpad = 0;
+    GridDev* d_grids = nullptr;
+    double* d_otab_d = nullptr;
+    float2* d_otab_f = nullptr;
+    size_t otab_cap = 0;
+    size_t grid_cap = 0;
+    // state
+    StateBuf st[2] = {};
+    int cur = 0;
+    double* d_R64 = nullptr;
+    double* d_ccr64 = nullptr;
+    double* d_cca64 = nullptr;
+    // binning scratch
+    uint32_t* d_key = nullptr;
+    uint32_t* d_slot = nullptr;
+    uint32_t* d_vkey_s = nullptr;
+    uint32_t* d_perm = nullptr;
+    unsigned long long* d_tmp = nullptr;
+    uint32_t* d_count[2] = {nullptr, nullptr};
+    uint32_t* d_start = nullptr;
+    uint32_t* d_bsum = nullptr;
+    size_t vcap = 0;  // capacity (entries) of count/start
+    double* d_io = nullptr;  // 6n doubles of staging
+    float* d_vout_f = nullptr;
+    double* d_vout_d = nullptr;
+    bool vout_valid = false;
+    uint32_t* d_err = nullptr;
+    bool keys_valid = false;
+    int64_t step = 0;
+    int force_block = 256;
+    int force_grid = 0;
+    int elem_grid = 0;
+    // graphs: one per starting parity of `cur`
+    int graph_steps = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    size_t dev_bytes = 0;
+    std::vector<void*> allocs;
+    // per-phase profiling: kProfPhases + 1 events per recorded step
+    static constexpr int kProfPhases = 4;
+    static constexpr int kProfCap = 4096;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_steps = 0;
+
+    ~mech() {
+        for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+        for (int p = 0; p < 2; ++p)
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+        for (void* p : allocs) cudaFree(p);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+
+    template <typename T>
+    int alloc(T** p, size_t count) {
+        *p = nullptr;
+        size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MECH_E_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                        cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        dev_bytes += bytes;
+        *p = static_cast<T*>(q);
+        return MECH_OK;
+    }
+
+    void free_ptr(void* p, size_t bytes) {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) allocs.erase(it);
+        cudaFree(p);
+        dev_bytes -= bytes;
+    }
+
+    void invalidate_graphs() {
+        for (int p = 0; p < 2; ++p)
+            if (gexec[p]) {
+                cudaGraphExecDestroy(gexec[p]);
+                gexec[p] = nullptr;
+            }
+    }
+
+    StepArgs args(int a_idx, int integrate) const {
+        StepArgs a{};
+        a.mode = mode;
+        a.n = (uint32_t)n;
+        a.npad = npad;
+        a.nrep = nrep;
+        a.grids = d_grids;
+        a.otab_d = d_otab_d;
+        a.otab_f = d_otab_f;
+        a.A = st[a_idx];
+        a.B = st[a_idx ^ 1];
+        a.key = d_key;
+        a.slot = d_slot;
+        a.vkey_s = d_vkey_s;
+        a.perm = d_perm;
+        a.tmp = d_tmp;
+        a.count_cur = d_count[a_idx];
+        a.count_nxt = d_count[a_idx ^ 1];
+        a.start = d_start;
+        a.R64 = d_R64;
+        a.ccr64 = d_ccr64;
+        a.cca64 = d_cca64;
+        a.A_f = (float)A;
+        a.dt_f = (float)dt;
+        a.A_d = A;
+        a.dt_d = dt;
+        a.integrate = integrate;
+        a.vout_f = d_vout_f;
+        a.vout_d = d_vout_d;
+        a.err = d_err;
+        return a;
+    }
+};
+
+namespace {
+
+int check_handle(mech_t* h) {
+    if (!h) return fail(MECH_E_ARG, "null handle");
+    return MECH_OK;
+}
+
+double voxel_of(const mech_t* h) { return h->voxel_int > 0.0 ? h->voxel_int : h->voxel_user; }
+
+// Build the per-replicate grids for the current voxel side and domains, and
+// size the voxel arrays.  Called outside the step loop only.
+int build_grids(mech_t* h) {
+    const double vx = voxel_of(h);
+    std::vector<GridDev> g(h->nrep);
+    std::vector<double> otd;
+    uint64_t vsum = 0;
+    for (int r = 0; r < h->nrep; ++r) {
+        double lo[3], hi[3];
+        if (h->dom_auto[r]) {
+            double half = std::max(1.5 * h->maxabs[r], 0.5 * vx);
+            for (int d = 0; d < 3; ++d) { lo[d] = -half; hi[d] = half; }
+        } else {
+            for (int d = 0; d < 3; ++d) { lo[d] = h->dom_lo[r][d]; hi[d] = h->dom_hi[r][d]; }
+        }
+        GridDev& G = g[r];
+        for (int d = 0; d < 3; ++d) {
+            double nd = std::ceil((hi[d] - lo[d]) / vx);
+            if (!(nd >= 1.0)) nd = 1.0;
+            if (nd > (double)(1 << 21)) return fail(MECH_E_OOM, "grid has more than 2^21 voxels along an axis");
+            G.n[d] = (int32_t)nd;
+            G.lo[d] = lo[d];
+            G.lo_f[d] = (float)lo[d];
+            G.tab[d] = (uint32_t)otd.size();
+            for (int i = 0; i < G.n[d]; ++i) otd.push_back(lo[d] + (double)i * vx);
+        }
+        G.h = vx;
+        G.inv_h = 1.0 / vx;
+        G.h_f = (float)vx;
+        G.inv_h_f = (float)(1.0 / vx);
+        G.vbase = (uint32_t)vsum;
+        G.cbase = (uint32_t)h->cbase[r];
+        G.ncell = (uint32_t)h->counts[r];
+        vsum += (uint64_t)G.n[0] * (uint64_t)G.n[1] * (uint64_t)G.n[2];
+        if (vsum > (uint64_t)0x7FFFFFFF - 2 * (uint64_t)kScanTile)
+            return fail(MECH_E_OOM, "voxel grids exceed 2^31 voxels; enlarge the voxel or shrink the domain");
+    }
+    const uint32_t V = (uint32_t)vsum;
+    const size_t Vpad = ((size_t)V + 1 + kScanTile - 1) / kScanTile * kScanTile;
+    // (re)allocate voxel arrays if they grew
+    if (Vpad > h->vcap) {
+        for (int p = 0; p < 2; ++p) h->free_ptr(h->d_count[p], h->vcap * 4);
+        h->free_ptr(h->d_start, h->vcap * 4);
+        h->free_ptr(h->d_bsum, h->vcap / kScanTile * 4);
+        h->d_count[0] = h->d_count[1] = nullptr;
+        h->d_start = nullptr;
+        h->d_bsum = nullptr;
+        h->vcap = 0;
+        MECH_TRY(h->alloc(&h->d_count[0], Vpad));
+        MECH_TRY(h->alloc(&h->d_count[1], Vpad));
+        MECH_TRY(h->alloc(&h->d_start, Vpad));
+        MECH_TRY(h->alloc(&h->d_bsum, Vpad / kScanTile));
+        h->vcap = Vpad;
+    }
+    if ((size_t)h->nrep > h->grid_cap) {
+        h->free_ptr(h->d_grids, h->grid_cap * sizeof(GridDev));
+        h->d_grids = nullptr;
+        MECH_TRY(h->alloc(&h->d_grids, (size_t)h->nrep));
+        h->grid_cap = h->nrep;
+    }
+    if (otd.size() > h->otab_cap) {
+        h->free_ptr(h->d_otab_d, h->otab_cap * sizeof(double));
+        h->free_ptr(h->d_otab_f, h->otab_cap * sizeof(float2));
+        h->d_otab_d = nullptr;
+        h->d_otab_f = nullptr;
+        MECH_TRY(h->alloc(&h->d_otab_d, otd.size()));
+        MECH_TRY(h->alloc(&h->d_otab_f, otd.size()));
+        h->otab_cap = otd.size();
+    }
+    std::vector<float2> otf(otd.size());
+    for (size_t i = 0; i < otd.size(); ++i) {
+        float hi = (float)otd[i];
+        otf[i] = make_float2(hi, (float)(otd[i] - (double)hi));
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_grids, g.data(), g.size() * sizeof(GridDev), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_otab_d, otd.data(), otd.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_otab_f, otf.data(), otf.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_count[0], Vpad, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_count[1], Vpad, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));  // host vectors die here
+    h->grids = g;
+    h->V = V;
+    h->Vpad = (uint32_t)Vpad;
+    h->grid_dirty = false;
+    h->keys_valid = false;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int ready(mech_t* h) {
+    MECH_TRY(check_handle(h));
+    if (!h->params_set) return fail(MECH_E_STATE, "mech_set_params must be called before stepping");
+    if (h->grid_dirty) MECH_TRY(build_grids(h));
+    return MECH_OK;
+}
+
+int ensure_keys(mech_t* h) {
+    if (h->keys_valid) return MECH_OK;
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_zero_u32(h->d_count[h->cur], h->Vpad, h->stream));
+    CUDA_TRY(launch_keys(a, h->elem_grid, h->stream));
+    h->keys_valid = true;
+    return MECH_OK;
+}
+
+// Enqueue one step from st[cur]; flips cur.  Needs valid keys.
+int enqueue_step(mech_t* h, int integrate, bool profile = false) {
+    StepArgs a = h->args(h->cur, integrate);
+    cudaEvent_t* ev = nullptr;
+    if (profile && h->prof_steps < mech::kProfCap) ev = &h->prof_ev[(size_t)h->prof_steps * (mech::kProfPhases + 1)];
+    if (ev) CUDA_TRY(cudaEventRecord(ev[0], h->stream));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, a.count_nxt, h->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[1], h->stream));
+    CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[2], h->stream));
+    CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[3], h->stream));
+    CUDA_TRY(launch_force(a, h->force_grid, h->force_block, h->stream));
+    if (ev) {
+        CUDA_TRY(cudaEventRecord(ev[4], h->stream));
+        ++h->prof_steps;
+    }
+    h->cur ^= 1;
+    return MECH_OK;
+}
+
+int capture_graph(mech_t* h) {
+    const int parity = h->cur;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MECH_OK;
+    for (int s = 0; s < h->graph_steps && rc == MECH_OK; ++s) rc = enqueue_step(h, 1);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->cur = parity;  // capture only recorded the launches
+    if (rc != MECH_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(MECH_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MECH_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return MECH_OK;
+}
+
+int check_err_flag(mech_t* h) {
+    uint32_t e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (e) {
+        cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
+        cudaStreamSynchronize(h->stream);
+        return fail(MECH_E_DEVICE_FLAG, std::string("device error flag raised: ") +
+                                            ((e & kErrNonFinite) ? "non-finite position or velocity " : "") +
+                                            ((e & kErrIndex) ? "index out of range" : ""));
+    }
+    return MECH_OK;
+}
+
+int validate_cells(int64_t n, const double* xyz, const double* R, const double* ccr, const double* cca) {
+    if (n < 0) return fail(MECH_E_ARG, "negative cell count");
+    if (n > 0 && (!xyz || !R || !ccr || !cca)) return fail(MECH_E_ARG, "null input array");
+    if (n >= (int64_t)0x7FFFFFFF) return fail(MECH_E_ARG, "more than 2^31-1 cells");
+    if (!finite_all(xyz, 3 * (size_t)n) || !finite_all(R, n) || !finite_all(ccr, n) || !finite_all(cca, n))
+        return fail(MECH_E_NONFINITE, "non-finite value in the cell arrays");
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(R[i] > 0.0)) return fail(MECH_E_ARG, "radius must be > 0 (cell " + std::to_string(i) + ")");
+        if (ccr[i] < 0.0 || cca[i] < 0.0)
+            return fail(MECH_E_ARG, "ccr and cca must be >= 0 (cell " + std::to_string(i) + ")");
+    }
+    return MECH_OK;
+}
+
+int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double* xyz, const double* R,
+                const double* ccr, const double* cca) {
+    int64_t n = 0;
+    for (int r = 0; r < nrep; ++r) {
+        if (counts[r] < 0) return fail(MECH_E_ARG, "negative replicate count");
+        n += counts[r];
+    }
+    MECH_TRY(validate_cells(n, xyz, R, ccr, cca));
+    mech_t* h = new (std::nothrow) mech_t();
+    if (!h) return fail(MECH_E_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        delete h;
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&h->dev);
+    if (e != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, h->dev);
+    if (e != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e)));
+    h->sms = prop.multiProcessorCount;
+    e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    h->stream = h->own_stream;
+    h->n = n;
+    h->nrep = nrep;
+    h->npad = (uint32_t)((n + 63) / 64 * 64);
+    if (h->npad == 0) h->npad = 64;
+    h->counts.assign(counts, counts + nrep);
+    h->cbase.resize(nrep);
+    int64_t run = 0;
+    for (int r = 0; r < nrep; ++r) { h->cbase[r] = run; run += counts[r]; }
+    h->dom_lo.assign(nrep, {0, 0, 0});
+    h->dom_hi.assign(nrep, {0, 0, 0});
+    h->dom_auto.assign(nrep, true);
+    h->maxabs.assign(nrep, 0.0);
+    for (int r = 0; r < nrep; ++r)
+        for (int64_t i = h->cbase[r]; i < h->cbase[r] + counts[r]; ++i)
+            for (int d = 0; d < 3; ++d) h->maxabs[r] = std::max(h->maxabs[r], std::fabs(xyz[3 * i + d]));
+    for (int64_t i = 0; i < n; ++i) h->maxR = std::max(h->maxR, R[i]);
+
+    const size_t np = h->npad;
+    int rc = MECH_OK;
+    for (int s = 0; s < 2 && rc == MECH_OK; ++s) {
+        StateBuf& b = h->st[s];
+        rc = h->alloc(&b.pos64, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&b.posf, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&b.comp, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&b.vp64, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&b.vpf, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&b.id, np);
+        if (rc == MECH_OK) rc = h->alloc(&b.cand, np);
+        if (rc == MECH_OK) rc = h->alloc(&b.candp, np);
+    }
+    if (rc == MECH_OK) rc = h->alloc(&h->d_R64, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_ccr64, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_cca64, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_key, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_slot, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_vkey_s, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_perm, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_tmp, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_io, 6 * np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_vout_f, 3 * np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_vout_d, 3 * np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_err, 1);
+    if (rc != MECH_OK) return bail(rc);
+
+    // caller order = initial state order; parameters and ids
+    std::vector<uint32_t> ids(n);
+    std::vector<float4> cand(n);
+    std::vector<float2> candp(n);
+    for (int64_t i = 0; i < n; ++i) {
+        ids[i] = (uint32_t)i;
+        cand[i] = make_float4(0.f, 0.f, 0.f, (float)R[i]);
+        candp[i] = make_float2((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]));
+    }
+    cudaStream_t s = h->stream;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    cudaError_t ce = cudaSuccess;
+    if (ce == cudaSuccess) ce = up(h->st[0].id, ids.data(), n * 4);
+    if (ce == cudaSuccess) ce = up(h->st[0].cand, cand.data(), n * sizeof(float4));
+    if (ce == cudaSuccess) ce = up(h->st[0].candp, candp.data(), n * sizeof(float2));
+    if (ce == cudaSuccess) ce = up(h->d_R64, R, n * 8);
+    if (ce == cudaSuccess) ce = up(h->d_ccr64, ccr, n * 8);
+    if (ce == cudaSuccess) ce = up(h->d_cca64, cca, n * 8);
+    if (ce == cudaSuccess) ce = up(h->d_io, xyz, 3 * n * 8);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->d_err, 0, 4, s);
+    if (ce != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("upload: ") + cudaGetErrorString(ce)));
+    StepArgs a = h->args(0, 1);
+    ce = launch_load_pos(a, h->st[0], h->d_io, 0, nullptr, s);
+    if (ce == cudaSuccess) ce = launch_load_vprev(a, h->st[0], nullptr, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("initial load: ") + cudaGetErrorString(ce)));
+    h->elem_grid = h->sms * 8;
+    h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
+    *out = h;
+    return MECH_OK;
+}
+
+// positions (value) and previous velocities of st[cur] -> device io buffers, caller order
+int stage_out(mech_t* h) {
+    StepArgs a = h->args(h->cur, 1);
+    const StateBuf& s = h->st[h->cur];
+    CUDA_TRY(launch_unpermute_pos(a, s, h->d_io, h->stream));
+    if (h->mode == kFP64)
+        CUDA_TRY(launch_unpermute_vel(a, s, nullptr, s.vp64, h->d_io + 3 * (size_t)h->npad, h->stream));
+    else
+        CUDA_TRY(launch_unpermute_vel(a, s, s.vpf, nullptr, h->d_io + 3 * (size_t)h->npad, h->stream));
+    return MECH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mech_last_error(void) { return g_err.c_str(); }
+
+int mech_version(void) { return 100; }
+
+int mech_create(mech_t** h, int64_t n, const double* xyz, const double* R, const double* ccr, const double* cca,
+                const int32_t* type) {
+    (void)type;
+    if (!h) return fail(MECH_E_ARG, "null output handle pointer");
+    *h = nullptr;
+    return create_impl(h, 1, &n, xyz, R, ccr, cca);
+}
+
+int mech_create_batch(mech_t** h, int32_t n_rep, const int64_t* counts, const double* xyz, const double* R,
+                      const double* ccr, const double* cca, const int32_t* type) {
+    (void)type;
+    if (!h) return fail(MECH_E_ARG, "null output handle pointer");
+    *h = nullptr;
+    if (n_rep < 1 || !counts) return fail(MECH_E_ARG, "n_rep must be >= 1 with a counts array");
+    return create_impl(h, n_rep, counts, xyz, R, ccr, cca);
+}
+
+int mech_set_params(mech_t* h, double A, double voxel_size, double dt) {
+    MECH_TRY(check_handle(h));
+    if (!std::isfinite(A) || !std::isfinite(voxel_size) || !std::isfinite(dt))
+        return fail(MECH_E_NONFINITE, "non-finite parameter");
+    if (!(A >= 1.0)) return fail(MECH_E_ARG, "adhesion factor A must be >= 1");
+    if (!(dt > 0.0)) return fail(MECH_E_ARG, "dt must be > 0");
+    if (!(voxel_size > 0.0)) return fail(MECH_E_ARG, "voxel_size must be > 0");
+    if (voxel_size < 2.0 * A * h->maxR)
+        return fail(MECH_E_VOXEL_TOO_SMALL, "voxel_size must be >= 2 A max R = " + std::to_string(2.0 * A * h->maxR));
+    if (h->voxel_int > 0.0 && h->voxel_int < 2.0 * A * h->maxR * (1.0 + 1e-6)) h->voxel_int = 0.0;
+    if (voxel_size != h->voxel_user || voxel_of(h) != voxel_size) h->grid_dirty = true;
+    h->A = A;
+    h->voxel_user = voxel_size;
+    h->dt = dt;
+    h->params_set = true;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_set_domain(mech_t* h, int32_t rep, const double lo[3], const double hi[3]) {
+    MECH_TRY(check_handle(h));
+    if (!lo || !hi) return fail(MECH_E_ARG, "null domain corner");
+    if (rep < -1 || rep >= h->nrep) return fail(MECH_E_ARG, "replicate index out of range");
+    for (int d = 0; d < 3; ++d) {
+        if (!std::isfinite(lo[d]) || !std::isfinite(hi[d])) return fail(MECH_E_NONFINITE, "non-finite domain");
+        if (!(hi[d] > lo[d])) return fail(MECH_E_ARG, "domain needs lo < hi on every axis");
+    }
+    for (int r = (rep < 0 ? 0 : rep); r < (rep < 0 ? h->nrep : rep + 1); ++r) {
+        h->dom_auto[r] = false;
+        for (int d = 0; d < 3; ++d) { h->dom_lo[r][d] = lo[d]; h->dom_hi[r][d] = hi[d]; }
+    }
+    h->grid_dirty = true;
+    if (h->params_set) return build_grids(h);
+    return MECH_OK;
+}
+
+int mech_set_internal_voxel(mech_t* h, double voxel) {
+    MECH_TRY(check_handle(h));
+    if (!std::isfinite(voxel)) return fail(MECH_E_NONFINITE, "non-finite voxel");
+    if (voxel != 0.0) {
+        if (!h->params_set) return fail(MECH_E_STATE, "mech_set_params must come first");
+        if (voxel < 2.0 * h->A * h->maxR * (1.0 + 1e-6))
+            return fail(MECH_E_VOXEL_TOO_SMALL, "internal voxel must be >= 2 A max R (1 + 1e-6)");
+    }
+    h->voxel_int = voxel;
+    h->grid_dirty = true;
+    if (h->params_set) return build_grids(h);
+    return MECH_OK;
+}
+
+int mech_set_launch(mech_t* h, int32_t force_block) {
+    MECH_TRY(check_handle(h));
+    if (force_block == 0) force_block = 256;
+    if (force_block < 32 || force_block > 256 || force_block % 32)
+        return fail(MECH_E_ARG, "force_block must be a multiple of 32 in [32, 256]");
+    h->force_block = force_block;
+    h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_set_stream(mech_t* h, void* stream) {
+    MECH_TRY(check_handle(h));
+    cudaStreamSynchronize(h->stream);
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return MECH_OK;
+}
+
+int mech_set_graph(mech_t* h, int32_t steps_per_graph) {
+    MECH_TRY(check_handle(h));
+    if (steps_per_graph < 0 || steps_per_graph % 2 || steps_per_graph > 100000)
+        return fail(MECH_E_ARG, "steps_per_graph must be 0 or an even number <= 100000");
+    h->graph_steps = steps_per_graph;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_set_precision(mech_t* h, int mode) {
+    MECH_TRY(check_handle(h));
+    if (mode != MECH_FP64 && mode != MECH_MIXED_FP64POS && mode != MECH_MIXED_KAHAN)
+        return fail(MECH_E_ARG, "unknown precision mode");
+    if (mode == h->mode) return MECH_OK;
+    // value of positions and previous velocities -> io, switch, reload
+    MECH_TRY(stage_out(h));
+    h->mode = mode;
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_load_pos(a, h->st[h->cur], h->d_io, 0, nullptr, h->stream));
+    CUDA_TRY(launch_load_vprev(a, h->st[h->cur], h->d_io + 3 * (size_t)h->npad, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
+    h->keys_valid = false;
+    h->vout_valid = false;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_step(mech_t* h, int64_t n_steps) {
+    MECH_TRY(ready(h));
+    if (n_steps < 0) return fail(MECH_E_ARG, "negative step count");
+    if (n_steps == 0 || h->n == 0) {
+        h->step += n_steps;
+        return MECH_OK;
+    }
+    MECH_TRY(ensure_keys(h));
+    h->vout_valid = false;
+    while (!h->profiling && h->graph_steps > 0 && n_steps >= h->graph_steps) {
+        if (!h->gexec[h->cur]) MECH_TRY(capture_graph(h));
+        CUDA_TRY(cudaGraphLaunch(h->gexec[h->cur], h->stream));
+        n_steps -= h->graph_steps;
+        h->step += h->graph_steps;
+    }
+    for (int64_t s = 0; s < n_steps; ++s) {
+        MECH_TRY(enqueue_step(h, 1, h->profiling));
+        ++h->step;
+    }
+    return MECH_OK;
+}
+
+int mech_set_profiling(mech_t* h, int32_t enable) {
+    MECH_TRY(check_handle(h));
+    if (enable && h->prof_ev.empty()) {
+        h->prof_ev.resize((size_t)mech::kProfCap * (mech::kProfPhases + 1), nullptr);
+        for (cudaEvent_t& e : h->prof_ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->profiling = enable != 0;
+    h->prof_steps = 0;
+    return MECH_OK;
+}
+
+int mech_read_profile(mech_t* h, double* phase_ms, int64_t* steps) {
+    MECH_TRY(check_handle(h));
+    if (!phase_ms) return fail(MECH_E_ARG, "null output");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int p = 0; p < mech::kProfPhases; ++p) phase_ms[p] = 0.0;
+    for (int s = 0; s < h->prof_steps; ++s) {
+        cudaEvent_t* ev = &h->prof_ev[(size_t)s * (mech::kProfPhases + 1)];
+        for (int p = 0; p < mech::kProfPhases; ++p) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]));
+            phase_ms[p] += ms;
+        }
+    }
+    if (steps) *steps = h->prof_steps;
+    h->prof_steps = 0;
+    return MECH_OK;
+}
+
+int mech_sync(mech_t* h) {
+    MECH_TRY(check_handle(h));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return check_err_flag(h);
+}
+
+int mech_compute_velocities(mech_t* h, double* out3n) {
+    MECH_TRY(ready(h));
+    if (!out3n && h->n > 0) return fail(MECH_E_ARG, "null output");
+    if (h->n == 0) return MECH_OK;
+    MECH_TRY(ensure_keys(h));
+    MECH_TRY(enqueue_step(h, 0));
+    h->vout_valid = true;
+    StepArgs a = h->args(h->cur, 0);
+    const StateBuf& s = h->st[h->cur];
+    if (h->mode == kFP64)
+        CUDA_TRY(launch_unpermute_vel(a, s, nullptr, h->d_vout_d, h->d_io, h->stream));
+    else
+        CUDA_TRY(launch_unpermute_vel(a, s, h->d_vout_f, nullptr, h->d_io, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(out3n, h->d_io, 3 * (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream));
+    return mech_sync(h);
+}
+
+int mech_read_positions(mech_t* h, double* out3n) {
+    MECH_TRY(check_handle(h));
+    if (h->n == 0) return MECH_OK;
+    if (!out3n) return fail(MECH_E_ARG, "null output");
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(out3n, h->d_io, 3 * (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream));
+    return mech_sync(h);
+}
+
+int mech_read_velocities(mech_t* h, double* out3n) {
+    MECH_TRY(check_handle(h));
+    if (h->n == 0) return MECH_OK;
+    if (!out3n) return fail(MECH_E_ARG, "null output");
+    StepArgs a = h->args(h->cur, 1);
+    const StateBuf& s = h->st[h->cur];
+    if (h->vout_valid) {
+        if (h->mode == kFP64) CUDA_TRY(launch_unpermute_vel(a, s, nullptr, h->d_vout_d, h->d_io, h->stream));
+        else CUDA_TRY(launch_unpermute_vel(a, s, h->d_vout_f, nullptr, h->d_io, h->stream));
+    } else {
+        if (h->mode == kFP64) CUDA_TRY(launch_unpermute_vel(a, s, nullptr, s.vp64, h->d_io, h->stream));
+        else CUDA_TRY(launch_unpermute_vel(a, s, s.vpf, nullptr, h->d_io, h->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(out3n, h->d_io, 3 * (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream));
+    return mech_sync(h);
+}
+
+int mech_write_positions(mech_t* h, const double* xyz3n) {
+    MECH_TRY(check_handle(h));
+    if (h->n == 0) return MECH_OK;
+    if (!xyz3n) return fail(MECH_E_ARG, "null input");
+    CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz3n, 3 * (size_t)h->n * 8, cudaMemcpyHostToDevice, h->stream));
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_load_pos(a, h->st[h->cur], h->d_io, 0, nullptr, h->stream));
+    h->keys_valid = false;
+    h->vout_valid = false;
+    return MECH_OK;
+}
+
+int mech_read_state(mech_t* h, double* xyz, double* vprev, double* comp, int64_t* step) {
+    MECH_TRY(check_handle(h));
+    if (step) *step = h->step;
+    if (h->n == 0) return MECH_OK;
+    if (!xyz || !vprev) return fail(MECH_E_ARG, "null output");
+    StepArgs a = h->args(h->cur, 1);
+    const StateBuf& s = h->st[h->cur];
+    const size_t n3 = 3 * (size_t)h->n * 8;
+    double* io2 = h->d_io + 3 * (size_t)h->npad;
+    if (h->mode == kMixedKahan) CUDA_TRY(launch_unpermute_vel(a, s, s.posf, nullptr, h->d_io, h->stream));
+    else CUDA_TRY(launch_unpermute_vel(a, s, nullptr, s.pos64, h->d_io, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(xyz, h->d_io, n3, cudaMemcpyDeviceToHost, h->stream));
+    if (h->mode == kFP64) CUDA_TRY(launch_unpermute_vel(a, s, nullptr, s.vp64, io2, h->stream));
+    else CUDA_TRY(launch_unpermute_vel(a, s, s.vpf, nullptr, io2, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(vprev, io2, n3, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (comp) {
+        if (h->mode == kMixedKahan) {
+            CUDA_TRY(launch_unpermute_vel(a, s, s.comp, nullptr, h->d_io, h->stream));
+            CUDA_TRY(cudaMemcpyAsync(comp, h->d_io, n3, cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            std::memset(comp, 0, n3);
+        }
+    }
+    return mech_sync(h);
+}
+
+int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const double* comp, int64_t step) {
+    MECH_TRY(check_handle(h));
+    if (h->n > 0) {
+        if (!xyz || !vprev) return fail(MECH_E_ARG, "null input");
+        if (!finite_all(xyz, 3 * (size_t)h->n) || !finite_all(vprev, 3 * (size_t)h->n) ||
+            (comp && !finite_all(comp, 3 * (size_t)h->n)))
+            return fail(MECH_E_NONFINITE, "non-finite state");
+        const size_t n3 = 3 * (size_t)h->n * 8;
+        double* io2 = h->d_io + 3 * (size_t)h->npad;
+        StepArgs a = h->args(h->cur, 1);
+        CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz, n3, cudaMemcpyHostToDevice, h->stream));
+        if (comp && h->mode == kMixedKahan)
+            CUDA_TRY(cudaMemcpyAsync(io2, comp, n3, cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(launch_load_pos(a, h->st[h->cur], h->d_io, 1, (comp && h->mode == kMixedKahan) ? io2 : nullptr,
+                                 h->stream));
+        CUDA_TRY(cudaMemcpyAsync(io2, vprev, n3, cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(launch_load_vprev(a, h->st[h->cur], io2, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    h->step = step;
+    h->keys_valid = false;
+    h->vout_valid = false;
+    return MECH_OK;
+}
+
+int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order) {
+    MECH_TRY(ready(h));
+    if (h->n == 0) {
+        if (count) std::memset(count, 0, (size_t)h->V * 4);
+        if (start) std::memset(start, 0, ((size_t)h->V + 1) * 4);
+        return MECH_OK;
+    }
+    h->keys_valid = false;
+    MECH_TRY(ensure_keys(h));
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, h->stream));
+    CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
+    CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
+    const size_t n = (size_t)h->n;
+    std::vector<uint32_t> k(n), ids(n), perm(n);
+    CUDA_TRY(cudaMemcpyAsync(k.data(), h->d_key, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(ids.data(), h->st[h->cur].id, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(perm.data(), h->d_perm, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (count) CUDA_TRY(cudaMemcpyAsync(count, a.count_cur, (size_t)h->V * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (start) CUDA_TRY(cudaMemcpyAsync(start, h->d_start, ((size_t)h->V + 1) * 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (key)
+        for (size_t i = 0; i < n; ++i) key[ids[i]] = k[i];
+    if (order)
+        for (size_t f = 0; f < n; ++f) order[f] = ids[perm[f]];
+    return check_err_flag(h);
+}
+
+int mech_info(mech_t* h, mech_info_t* out) {
+    MECH_TRY(check_handle(h));
+    if (!out) return fail(MECH_E_ARG, "null output");
+    if (h->params_set && h->grid_dirty) MECH_TRY(build_grids(h));
+    std::memset(out, 0, sizeof(*out));
+    out->n_cells = h->n;
+    out->n_rep = h->nrep;
+    out->mode = h->mode;
+    out->n_voxels = h->V;
+    if (!h->grids.empty())
+        for (int d = 0; d < 3; ++d) out->dims[d] = h->grids[0].n[d];
+    out->voxel = voxel_of(h);
+    out->step = h->step;
+    out->launches_per_step = h->n > 0 ? 6 : 0;
+    out->graph_steps = h->graph_steps;
+    out->device_bytes = (int64_t)h->dev_bytes;
+    return MECH_OK;
+}
+
+int mech_grid(mech_t* h, int32_t rep, double* lo3, int32_t* dims3, int64_t* voxel_base) {
+    MECH_TRY(check_handle(h));
+    if (rep < 0 || rep >= h->nrep) return fail(MECH_E_ARG, "replicate index out of range");
+    if (!h->params_set) return fail(MECH_E_STATE, "mech_set_params must come first");
+    if (h->grid_dirty) MECH_TRY(build_grids(h));
+    const GridDev& g = h->grids[rep];
+    for (int d = 0; d < 3; ++d) {
+        if (lo3) lo3[d] = g.lo[d];
+        if (dims3) dims3[d] = g.n[d];
+    }
+    if (voxel_base) *voxel_base = g.vbase;
+    return MECH_OK;
+}
+
+int mech_destroy(mech_t* h) {
+    if (!h) return MECH_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    return MECH_OK;
+}
+
+}  // extern "C"

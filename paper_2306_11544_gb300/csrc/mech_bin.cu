@@ -1,0 +1,340 @@
+// Binning kernels of the mechanics step: voxel keys + histogram, exclusive
+// scan, stable scatter into voxel order, and the host-order <-> voxel-order
+// copies used by the read/write calls.
+//
+// The counting sort is the GPU form of the paper's locality lesson (Sec. 5.4):
+// cells are re-stored every step in the order of the 3-D voxel mesh so that
+// spatial neighbours are memory neighbours, and a voxel costs work only in
+// proportion to the cells it holds.  Order inside a voxel is ascending caller
+// index, which makes the permutation a function of the positions alone.
+#include "mech_internal.cuh"
+
+namespace mk {
+
+namespace {
+
+__global__ void k_zero_u32(uint32_t* __restrict__ p, size_t count) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (; i < count; i += stride) p[i] = 0u;
+}
+
+// Step 1a (first step after a state change): key of every cell in A order and
+// its arrival slot inside its voxel.  Loop is warp-uniform so that the
+// aggregated atomics always run on full warps.
+__global__ void k_keys(const StepArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
+        const uint32_t i = base + lane;
+        const bool valid = i < a.n;
+        uint32_t key = 0;
+        if (valid) {
+            const int r = rep_of_cell(a.grids, a.nrep, i);
+            key = cell_key(a.mode, a.grids[r], a.A, a.npad, i);
+        }
+        const uint32_t slot = warp_count(a.count_cur, key, valid);
+        if (valid) {
+            a.key[i] = key;
+            a.slot[i] = slot;
+        }
+    }
+}
+
+// ---- exclusive scan of the histogram (reduce, scan of block sums, down-sweep) ----
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh_warp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? sh_warp[lane] : 0u;
+        uint32_t ws = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        if (lane < nw) sh_warp[lane] = ws - w;
+        if (lane == nw - 1) sh_warp[32] = ws;
+    }
+    __syncthreads();
+    uint32_t r = sh_warp[wid] + x - v;
+    *total = sh_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ count,
+                                                              uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t sh[33];
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+    const uint4* c4 = reinterpret_cast<const uint4*>(count + base);
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems / 4; ++k) {
+        uint4 q = c4[k * kScanThreads + threadIdx.x];
+        s += q.x + q.y + q.z + q.w;
+    }
+    uint32_t tot;
+    block_exclusive_scan(s, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// One block scans the block sums in place (exclusive).
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, uint32_t nb) {
+    __shared__ uint32_t sh[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(v, sh, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// start[v] = sum_{u<v} count[u]; each thread owns 16 consecutive voxels.  Also
+// clears the next step's histogram over the same range.
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ count,
+                                                            const uint32_t* __restrict__ boff,
+                                                            uint32_t* __restrict__ start,
+                                                            uint32_t* __restrict__ zero_next) {
+    __shared__ uint32_t sh[33];
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    const uint4* c4 = reinterpret_cast<const uint4*>(count + base);
+    uint4 q[kScanItems / 4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems / 4; ++k) {
+        q[k] = c4[k];
+        s += q[k].x + q[k].y + q[k].z + q[k].w;
+    }
+    uint32_t tot;
+    uint32_t run = boff[blockIdx.x] + block_exclusive_scan(s, sh, &tot);
+    uint4* s4 = reinterpret_cast<uint4*>(start + base);
+#pragma unroll
+    for (int k = 0; k < kScanItems / 4; ++k) {
+        uint4 o;
+        o.x = run; run += q[k].x;
+        o.y = run; run += q[k].y;
+        o.z = run; run += q[k].z;
+        o.w = run; run += q[k].w;
+        s4[k] = o;
+    }
+    if (zero_next) {
+        uint4* z4 = reinterpret_cast<uint4*>(zero_next + base);
+#pragma unroll
+        for (int k = 0; k < kScanItems / 4; ++k) z4[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Step 1c: every cell goes to start[key] + slot, carrying (id, A index).  The
+// slot order inside a voxel comes from atomics; k_canon makes it canonical.
+__global__ void k_scatter(const StepArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const uint32_t k = a.key[i];
+        const uint32_t dst = a.start[k] + a.slot[i];
+        a.tmp[dst] = ((unsigned long long)a.A.id[i] << 32) | (unsigned long long)i;
+    }
+}
+
+// Step 1d: rank each cell inside its voxel by caller index (ids are unique),
+// giving its final voxel-order position f; record perm[f], the key, and the
+// force-ready FP32 record of the cell (position relative to its own voxel
+// origin, radius, square roots of the coefficients).
+__global__ void k_canon(const StepArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const unsigned long long e = a.tmp[q];
+        const uint32_t id = (uint32_t)(e >> 32);
+        const uint32_t src = (uint32_t)e;
+        const uint32_t k = a.key[src];
+        const uint32_t s = a.start[k], en = a.start[k + 1];
+        uint32_t rank = 0;
+        for (uint32_t t = s; t < en; ++t) rank += (uint32_t)((uint32_t)(a.tmp[t] >> 32) < id);
+        const uint32_t f = s + rank;
+        a.perm[f] = src;
+        a.vkey_s[f] = k;
+        const int r = rep_of_cell(a.grids, a.nrep, f);
+        const GridDev& g = a.grids[r];
+        const uint32_t local = k - g.vbase;
+        const uint32_t ix = local % (uint32_t)g.n[0];
+        const uint32_t rest = local / (uint32_t)g.n[0];
+        const uint32_t iy = rest % (uint32_t)g.n[1];
+        const uint32_t iz = rest / (uint32_t)g.n[1];
+        const uint32_t ii[3] = {ix, iy, iz};
+        float p[3];
+        if (a.mode == kMixedKahan) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float xh = a.A.posf[(size_t)d * a.npad + src];
+                const float c = a.A.comp[(size_t)d * a.npad + src];
+                const float2 o = a.otab_f[g.tab[d] + ii[d]];
+                // (x_hi - c) - (o.hi + o.lo): x_hi - o.hi is exact for a cell in
+                // (or near) the voxel; the small terms are added afterwards.
+                p[d] = __fsub_rn(__fsub_rn(xh, o.x), __fadd_rn(o.y, c));
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double x = a.A.pos64[(size_t)d * a.npad + src];
+                p[d] = __double2float_rn(__dsub_rn(x, a.otab_d[g.tab[d] + ii[d]]));
+            }
+        }
+        const float R = reinterpret_cast<const float*>(a.A.cand)[4 * (size_t)src + 3];
+        a.B.cand[f] = make_float4(p[0], p[1], p[2], R);
+        a.B.candp[f] = a.A.candp[src];
+    }
+}
+
+// Voxel order -> caller order (positions), through the id of each slot.
+__global__ void k_unpermute_pos(const StepArgs a, const StateBuf st, double* __restrict__ out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = st.id[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x;
+            if (a.mode == kMixedKahan)
+                x = __dsub_rn((double)st.posf[(size_t)d * a.npad + q], (double)st.comp[(size_t)d * a.npad + q]);
+            else
+                x = st.pos64[(size_t)d * a.npad + q];
+            out[3 * (size_t)id + d] = x;
+        }
+    }
+}
+
+__global__ void k_unpermute_vel(const StepArgs a, const StateBuf st, const float* __restrict__ vf,
+                                const double* __restrict__ vd, double* __restrict__ out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = st.id[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            out[3 * (size_t)id + d] = vd ? vd[(size_t)d * a.npad + q] : (double)vf[(size_t)d * a.npad + q];
+    }
+}
+
+// Caller order -> current state order (positions).  raw_kahan: `in` holds the
+// FP32 x_hi values and comp_in the compensations (exact state reload);
+// otherwise `in` is a position value and the Kahan pair is built from it.
+__global__ void k_load_pos(const StepArgs a, const StateBuf st, const double* __restrict__ in, int raw_kahan,
+                           const double* __restrict__ comp_in) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = st.id[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = in[3 * (size_t)id + d];
+            if (a.mode == kMixedKahan) {
+                float xh, c;
+                if (raw_kahan) {
+                    xh = (float)x;
+                    c = comp_in ? (float)comp_in[3 * (size_t)id + d] : 0.0f;
+                } else {
+                    xh = __double2float_rn(x);
+                    c = __double2float_rn(__dsub_rn((double)xh, x));
+                }
+                st.posf[(size_t)d * a.npad + q] = xh;
+                st.comp[(size_t)d * a.npad + q] = c;
+            } else {
+                st.pos64[(size_t)d * a.npad + q] = x;
+            }
+        }
+    }
+}
+
+__global__ void k_load_vprev(const StepArgs a, const StateBuf st, const double* __restrict__ in) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = st.id[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = in ? in[3 * (size_t)id + d] : 0.0;
+            if (a.mode == kFP64) st.vp64[(size_t)d * a.npad + q] = v;
+            else st.vpf[(size_t)d * a.npad + q] = __double2float_rn(v);
+        }
+    }
+}
+
+int elementwise_grid(uint32_t n) {
+    int g = (int)((n + 255u) / 256u);
+    if (g < 1) g = 1;
+    if (g > 152 * 16) g = 152 * 16;
+    return g;
+}
+
+}  // namespace
+
+cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    int g = (int)((count + 255) / 256);
+    if (g > 152 * 32) g = 152 * 32;
+    k_zero_u32<<<g, 256, 0, s>>>(p, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_keys<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start, uint32_t* zero_next,
+                        cudaStream_t s) {
+    const uint32_t nb = vpad / kScanTile;
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(count, bsum);
+    k_scan_top<<<1, 1024, 0, s>>>(bsum, nb);
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, zero_next);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_scatter<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_canon<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_unpermute_pos<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const float* vf, const double* vd,
+                                 double* out, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_unpermute_vel<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, vf, vd, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double* in, int raw_kahan,
+                            const double* comp_in, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_load_pos<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, in, raw_kahan, comp_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_vprev(const StepArgs& a, const StateBuf& st, const double* in, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_load_vprev<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, in);
+    return cudaGetLastError();
+}
+
+}  // namespace mk

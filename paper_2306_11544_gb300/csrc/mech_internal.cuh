@@ -1,0 +1,178 @@
+// Internal declarations of libmech: device data layout, kernel argument
+// block and the launch wrappers of each translation unit.
+//
+// Data layout in HBM (one handle, n cells, V voxels over all replicates):
+//   * per-cell state, double-buffered (A = current order, B = the voxel order
+//     built this step), SoA with stride `npad` per component:
+//       pos64  [3][npad] double   positions (FP64 and FP64-position modes)
+//       posf   [3][npad] float    positions x_hi (Kahan mode)
+//       comp   [3][npad] float    Kahan compensation c, value = x_hi - c
+//       vp64   [3][npad] double   previous velocity (FP64 mode)
+//       vpf    [3][npad] float    previous velocity (mixed modes)
+//       id     [n]       u32      caller index of the cell
+//       cand   [n]       float4   {p_x, p_y, p_z, R}: p = position relative to
+//                                 the origin of the cell's own voxel, FP32
+//       candp  [n]       float2   {sqrt(ccr), sqrt(cca)}
+//   * binning scratch: key/slot [n] (key and within-voxel arrival slot of
+//     each cell in A order), vkey_s [n] (key in B order), perm [n] (A index of
+//     the cell at each B position), tmp [n] u64 (id << 32 | A index, scattered
+//     by key), count[2][Vpad] (histograms of this and the next step),
+//     start[Vpad] (exclusive scan of count: cells of voxel v are the sorted
+//     positions start[v] .. start[v+1]-1).
+//   * per-replicate grid descriptors and per-axis voxel-origin tables.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mk {
+
+enum Mode { kFP64 = 0, kMixedFP64Pos = 1, kMixedKahan = 2 };
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // voxels per scan block
+
+// Device error flag bits (the host reports any of them as MECH_E_DEVICE_FLAG).
+constexpr uint32_t kErrNonFinite = 1u;
+constexpr uint32_t kErrIndex = 2u;
+
+struct GridDev {
+    double lo[3];
+    double h, inv_h;   // voxel side and its FP64 reciprocal (1/h rounded once)
+    float lo_f[3];     // (float)lo
+    float h_f, inv_h_f;  // (float)h, (float)(1/h)
+    int32_t n[3];
+    uint32_t vbase;    // first global voxel index of this replicate
+    uint32_t cbase;    // first cell (same in caller and voxel order)
+    uint32_t ncell;
+    uint32_t tab[3];   // offset of each axis in the origin tables
+};
+
+struct StateBuf {
+    double* pos64;
+    float* posf;
+    float* comp;
+    double* vp64;
+    float* vpf;
+    uint32_t* id;
+    float4* cand;
+    float2* candp;
+};
+
+struct StepArgs {
+    int mode;
+    uint32_t n;
+    uint32_t npad;
+    int nrep;
+    const GridDev* grids;
+    const double* otab_d;  // voxel origin lo_d + i h per axis index, FP64
+    const float2* otab_f;  // the same origin as an exact FP32 pair (hi, lo)
+    StateBuf A, B;
+    uint32_t* key;
+    uint32_t* slot;
+    uint32_t* vkey_s;
+    uint32_t* perm;
+    unsigned long long* tmp;
+    uint32_t* count_cur;
+    uint32_t* count_nxt;
+    uint32_t* start;
+    const double* R64;    // FP64 parameters in caller order (FP64 mode)
+    const double* ccr64;
+    const double* cca64;
+    float A_f, dt_f;
+    double A_d, dt_d;
+    int integrate;         // 1: AB2 update; 0: velocities only (positions kept)
+    float* vout_f;         // velocities-only output, B order (mixed modes)
+    double* vout_d;        // velocities-only output, B order (FP64 mode)
+    uint32_t* err;
+};
+
+// ---- launch wrappers (mech_bin.cu) ----
+cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
+cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start,
+                        uint32_t* zero_next, cudaStream_t s);
+cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);
+cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const float* vf, const double* vd,
+                                 double* out, cudaStream_t s);
+cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double* in, int raw_kahan,
+                            const double* comp_in, cudaStream_t s);
+cudaError_t launch_load_vprev(const StepArgs& a, const StateBuf& st, const double* in, cudaStream_t s);
+cudaError_t launch_build_cand(const StepArgs& a, const StateBuf& st, cudaStream_t s);
+
+// ---- launch wrappers (mech_force.cu) ----
+cudaError_t launch_force(const StepArgs& a, int grid, int block, cudaStream_t s);
+int force_max_blocks_per_sm(int mode, int block);
+
+// ---- small device helpers shared by the kernel files ----
+__device__ __forceinline__ int rep_of_cell(const GridDev* g, int nrep, uint32_t q) {
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g[mid].cbase <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Voxel index along one axis from an FP64 coordinate: floor((x - lo) * inv_h)
+// with two IEEE roundings and no contraction, clamped into [0, n-1] (NaN -> 0).
+__device__ __forceinline__ int axis_index_f64(double x, double lo, double inv_h, int n) {
+    double t = __dmul_rn(__dsub_rn(x, lo), inv_h);
+    double f = floor(t);
+    if (!(f >= 0.0)) return 0;
+    if (f >= (double)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+// Same decision taken in FP32 (positions held in FP32, or rounded to FP32).
+__device__ __forceinline__ int axis_index_f32(float x, float lo, float inv_h, int n) {
+    float t = __fmul_rn(__fsub_rn(x, lo), inv_h);
+    float f = floorf(t);
+    if (!(f >= 0.0f)) return 0;
+    if (f >= (float)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Voxel key of the cell at state index i (positions in state buffer st).
+__device__ __forceinline__ uint32_t cell_key(int mode, const GridDev& g, const StateBuf& st, uint32_t npad,
+                                             uint32_t i) {
+    int ix, iy, iz;
+    if (mode == kFP64) {
+        ix = axis_index_f64(st.pos64[i], g.lo[0], g.inv_h, g.n[0]);
+        iy = axis_index_f64(st.pos64[npad + i], g.lo[1], g.inv_h, g.n[1]);
+        iz = axis_index_f64(st.pos64[2 * (size_t)npad + i], g.lo[2], g.inv_h, g.n[2]);
+    } else if (mode == kMixedFP64Pos) {
+        ix = axis_index_f32(__double2float_rn(st.pos64[i]), g.lo_f[0], g.inv_h_f, g.n[0]);
+        iy = axis_index_f32(__double2float_rn(st.pos64[npad + i]), g.lo_f[1], g.inv_h_f, g.n[1]);
+        iz = axis_index_f32(__double2float_rn(st.pos64[2 * (size_t)npad + i]), g.lo_f[2], g.inv_h_f, g.n[2]);
+    } else {
+        ix = axis_index_f32(st.posf[i], g.lo_f[0], g.inv_h_f, g.n[0]);
+        iy = axis_index_f32(st.posf[npad + i], g.lo_f[1], g.inv_h_f, g.n[1]);
+        iz = axis_index_f32(st.posf[2 * (size_t)npad + i], g.lo_f[2], g.inv_h_f, g.n[2]);
+    }
+    return g.vbase + (uint32_t)ix + (uint32_t)g.n[0] * ((uint32_t)iy + (uint32_t)g.n[1] * (uint32_t)iz);
+}
+
+// Warp-aggregated histogram increment: lanes with equal keys share one atomic.
+// All 32 lanes must call it; lanes with valid == false take no slot.
+__device__ __forceinline__ uint32_t warp_count(uint32_t* count, uint32_t key, bool valid) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t k = valid ? key : 0xFFFFFFFFu;
+    uint32_t grp = __match_any_sync(0xFFFFFFFFu, k);
+    uint32_t leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&count[key], (uint32_t)__popc(grp));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    return base + (uint32_t)__popc(grp & lanemask_lt());
+}
+
+}  // namespace mk

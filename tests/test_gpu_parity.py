@@ -1,0 +1,229 @@
+"""CUDA path against the oracle, element by element, on seeded inputs.
+
+Binning (keys, histogram, scan, permutation) must be bit-exact; FP64-mode
+velocities must match to 1e-5 (they are expected to be bit-identical, since
+the kernel evaluates the same operations in the same order); the FP32 pair
+arithmetic of the mixed modes must match to TOL_V_MIXED; final positions of
+the mixed modes to 1e-3 um."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_11544_gb300 import synth
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["fp64", "mixed", "kahan"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    H.lib()
+    oracle.build()
+
+
+def oracle_keys_for(m, pop, mode):
+    dims = H.dims_of(pop)
+    if mode == "fp64":
+        return oracle.keys(m.positions(), pop.lo, pop.h, dims)
+    if mode == "mixed":
+        return oracle.keys_f32(m.positions().astype(np.float32), pop.lo, pop.h, dims)
+    st = m.read_state()  # Kahan: the FP32 x_hi values decide the voxel
+    return oracle.keys_f32(st["xyz"].astype(np.float32), pop.lo, pop.h, dims)
+
+
+def check_bins(m, pop, mode):
+    key, count, start, order = m.bins()
+    kref = oracle_keys_for(m, pop, mode)
+    V = int(np.prod(H.dims_of(pop)))
+    cref, sref, oref = oracle.counting_sort(kref, V)
+    assert np.array_equal(key, kref)
+    assert np.array_equal(count, cref)
+    assert np.array_equal(start, sref)
+    assert np.array_equal(order, oref)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", list(H.parity_populations().keys()))
+def test_binning_bit_exact(name, mode):
+    pop = H.parity_populations()[name]
+    with H.make(pop, mode) as m:
+        check_bins(m, pop, mode)
+        m.step(3)  # and again after the fused next-step histogram
+        check_bins(m, pop, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", list(H.edge_populations().keys()))
+def test_edge_cases(name, mode):
+    pop = H.edge_populations()[name]
+    with H.make(pop, mode) as m:
+        check_bins(m, pop, mode)
+        x0 = m.positions()
+        v = m.compute_velocities()
+        vref = oracle.velocities(x0, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+        tol = H.TOL_V_FP64 if mode == "fp64" else H.TOL_V_MIXED
+        assert H.rel_err(v, vref) <= tol, (name, mode, H.rel_err(v, vref))
+        if np.abs(vref).max() == 0:
+            assert np.abs(v).max() == 0
+        assert np.all(np.isfinite(v))
+
+
+@pytest.mark.parametrize("name", list(H.parity_populations().keys()))
+def test_fp64_velocity(name):
+    pop = H.parity_populations()[name]
+    with H.make(pop, "fp64") as m:
+        v = m.compute_velocities()
+        vref = oracle.velocities(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+        err = H.rel_err(v, vref)
+        print(f"fp64 {name}: rel err {err:.3e}, bitwise equal: {np.array_equal(v, vref)}")
+        assert err <= H.TOL_V_FP64
+        assert np.array_equal(v, vref)  # same operations, same order
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+@pytest.mark.parametrize("name", list(H.parity_populations().keys()))
+def test_mixed_velocity_per_step(name, mode):
+    """A7: per-step velocity on identical input positions (the GPU state fed
+    to the oracle), over a few steps."""
+    pop = H.parity_populations()[name]
+    with H.make(pop, mode) as m:
+        for _ in range(3):
+            x = m.positions()
+            m.step(1)
+            v = m.velocities()
+            vref = oracle.velocities(x, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+            err = H.rel_err(v, vref)
+            print(f"{mode} {name}: per-step velocity rel err {err:.3e}")
+            assert err <= H.TOL_V_MIXED
+
+
+def test_fp64_trajectory_spheroid_2k():
+    """2,000 cells, FP64, the configuration's 100 steps, against the oracle."""
+    pop = synth.spheroid_2k(seed=0)
+    with H.make(pop, "fp64") as m:
+        m.step(pop.steps)
+        x = m.positions()
+        v = m.velocities()
+    xr, vpr, vr = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, pop.steps)
+    err = np.abs(x - xr).max()
+    print(f"fp64 spheroid_2k 100 steps: max |dx| = {err:.3e} um, bitwise: {np.array_equal(x, xr)}")
+    assert err <= 1e-9
+    assert H.rel_err(v, vr) <= H.TOL_V_FP64
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_mixed_trajectory_spheroid_2k(mode):
+    pop = synth.spheroid_2k(seed=0)
+    with H.make(pop, mode) as m:
+        m.step(pop.steps)
+        x = m.positions()
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, pop.steps)
+    err = np.abs(x - xr).max()
+    print(f"{mode} spheroid_2k 100 steps: max |dx| = {err:.3e} um")
+    assert err <= H.TOL_X_MIXED
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_mixed_trajectory_spheroid_1m_scaled(mode):
+    """Three cell types with lognormal radii (20k cells, same density as the
+    1M-cell spheroid), 300 steps."""
+    pop = synth.spheroid_1m(seed=1, scale=0.02)
+    steps = 300
+    with H.make(pop, mode) as m:
+        m.step(steps)
+        x = m.positions()
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, steps)
+    err = np.abs(x - xr).max()
+    print(f"{mode} spheroid_1m x0.02 {steps} steps: max |dx| = {err:.3e} um")
+    assert err <= H.TOL_X_MIXED
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_graph_replay_is_bitwise_identical(mode):
+    pop = synth.clustered_20m(seed=3, scale=0.0005)
+    with H.make(pop, mode) as a, H.make(pop, mode, graph=4) as b:
+        a.step(11)
+        b.step(11)
+        sa, sb = a.read_state(), b.read_state()
+    for k in ("xyz", "vprev", "comp"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_checkpoint_resume_is_bitwise(mode):
+    pop = synth.spheroid_1m(seed=4, scale=0.005)
+    with H.make(pop, mode) as a:
+        a.step(7)
+        saved = a.read_state()
+        a.step(6)
+        full = a.read_state()
+    with H.make(pop, mode) as b:
+        b.load_state(saved)
+        b.step(6)
+        resumed = b.read_state()
+    assert resumed["step"] == full["step"] == 13
+    for k in ("xyz", "vprev", "comp"):
+        assert np.array_equal(resumed[k], full[k]), k
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_internal_voxel_keeps_the_pair_set(mode):
+    """A finer internal voxel (>= 2 A max R) changes only the FP32 order."""
+    pop = synth.clustered_20m(seed=5, scale=0.001)
+    with H.make(pop, mode) as m:
+        v30 = m.compute_velocities()
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    with H.make(pop, mode, voxel=hmin) as m:
+        vmin = m.compute_velocities()
+    vref = oracle.velocities(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert H.rel_err(v30, vref) <= H.TOL_V_MIXED
+    assert H.rel_err(vmin, vref) <= H.TOL_V_MIXED
+
+
+def test_empty_population():
+    pop = H.tiny_population(np.zeros((0, 3)), [-60] * 3, [60] * 3)
+    with H.make(pop, "mixed") as m:
+        m.step(5)
+        assert m.positions().shape == (0, 3)
+        assert m.info()["step"] == 5
+
+
+def test_precision_switch_round_trip():
+    pop = synth.spheroid_2k(seed=6)
+    with H.make(pop, "fp64") as m:
+        m.step(3)
+        x = m.positions()
+        m.set_precision("kahan")
+        assert np.abs(m.positions() - x).max() <= 1e-4
+        m.set_precision("fp64")
+        assert np.abs(m.positions() - x).max() <= 1e-4
+
+
+def test_write_positions_then_step_matches_fresh_handle():
+    pop = synth.spheroid_2k(seed=7)
+    rng = np.random.Generator(np.random.PCG64(8))
+    moved = pop.xyz + rng.normal(0, 0.5, size=pop.xyz.shape)
+    with H.make(pop, "fp64") as m:
+        m.write_positions(moved)
+        v = m.compute_velocities()
+    vref = oracle.velocities(moved, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert np.array_equal(v, vref)
+
+
+def test_nonfinite_state_raises_device_flag():
+    """A cell pushed to a non-finite position is reported, not hidden (the
+    fault is made on the host: positions written with a huge value overflow
+    in the update)."""
+    from paper_2306_11544_gb300 import mech
+    pop = H.tiny_population([[0.0, 0.0, 0.0], [1e-30, 0.0, 0.0]], [-60] * 3, [60] * 3)
+    with H.make(pop, "fp64") as m:
+        m.write_positions(np.array([[0.0, 0.0, 0.0], [1.7e308, 0.0, 0.0]]))
+        m.set_params(1.25, 30.0, 1e308)
+        m.load_state({"xyz": np.array([[0.0, 0.0, 0.0], [1.7e308, 0.0, 0.0]]),
+                      "vprev": np.array([[0.0, 0.0, 0.0], [-1e308, 0.0, 0.0]]), "step": 0})
+        m.step(1)
+        with pytest.raises(mech.MechError) as e:
+            m.sync()
+        assert e.value.code == mech.MECH_E_DEVICE_FLAG
