@@ -195,6 +195,36 @@ MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, 
  */
 MECH_API int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order);
 
+/*
+ * Binning without allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they call it --
+ * code whose device memory is already entirely reserved by another allocator
+ * (a framework's caching pool that owns the GPU), or a latency-critical loop
+ * that cannot afford cudaMalloc's implicit device synchronisation.  It runs
+ * the binning of step 1 for one grid, with the voxel index taken in FP64 as in
+ * MECH_FP64 mode and the cells of a voxel in ascending input index:
+ *   xyz    device, 3n doubles (interleaved): positions;
+ *   lo, voxel, dims  host: grid lower corner, voxel side, voxels per axis;
+ *   key    device, n u32: voxel key of each cell, input order;
+ *   start  device, V + 1 u32, V = dims[0] dims[1] dims[2]: exclusive prefix
+ *          sum of the voxel counts (cells of voxel v are start[v]..start[v+1]-1);
+ *   order  device, n u32: input index of the cell at each sorted position;
+ *   stream a cudaStream_t (NULL: the legacy default stream).
+ * Limits: n <= 262,144 and V <= 524,288; larger sizes return MECH_E_ARG and
+ * launch nothing.  The working memory is a fixed array of about 6.1 MiB in the
+ * library's device data, held by every GPU that loads the library until the
+ * process exits; the call itself allocates and frees nothing.  The first call
+ * on each device looks up the device address of that array
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Asynchronous: the outputs are ready when the
+ * stream reaches this work.  Every call uses the same array and leaves its
+ * contents behind, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and corrupt each other's results: serialise them.
+ */
+MECH_API int mech_bin_noalloc(int64_t n, const double* xyz, const double lo[3], double voxel,
+                              const int32_t dims[3], uint32_t* key, uint32_t* start, uint32_t* order,
+                              void* stream);
+
 typedef struct {
     int64_t n_cells;
     int32_t n_rep;

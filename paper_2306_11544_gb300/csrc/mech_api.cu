@@ -45,6 +45,8 @@ bool finite_all(const double* p, size_t n) {
 
 }  // namespace
 
+int mk::record_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct mech {
     int dev = 0;
     int sms = 152;

@@ -23,6 +23,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace mk {
@@ -102,6 +104,9 @@ cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double*
                             const double* comp_in, cudaStream_t s);
 cudaError_t launch_load_vprev(const StepArgs& a, const StateBuf& st, const double* in, cudaStream_t s);
 cudaError_t launch_build_cand(const StepArgs& a, const StateBuf& st, cudaStream_t s);
+
+// ---- error reporting of the C ABI (mech_api.cu): sets mech_last_error ----
+int record_error(int code, const std::string& msg);
 
 // ---- launch wrappers (mech_force.cu) ----
 cudaError_t launch_force(const StepArgs& a, int grid, int block, cudaStream_t s);

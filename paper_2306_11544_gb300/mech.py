@@ -43,7 +43,7 @@ EXPORTS = [
     "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
-    "mech_load_state", "mech_debug_bins", "mech_info", "mech_grid", "mech_destroy",
+    "mech_load_state", "mech_debug_bins", "mech_bin_noalloc", "mech_info", "mech_grid", "mech_destroy",
 ]
 
 
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
             "mech_read_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_load_state": ([_P, _P, _P, _P, ctypes.c_int64], ctypes.c_int),
             "mech_debug_bins": ([_P, _P, _P, _P, _P], ctypes.c_int),
+            "mech_bin_noalloc": ([ctypes.c_int64, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P], ctypes.c_int),
             "mech_info": ([_P, _P], ctypes.c_int),
             "mech_grid": ([_P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
             "mech_destroy": ([_P], ctypes.c_int),
@@ -291,6 +292,18 @@ def mech_debug_bins(h, n):
     order = np.empty(n, dtype=np.int64)
     _check(load_library().mech_debug_bins(h, _ptr(key), _ptr(count), _ptr(start), _ptr(order)), "mech_debug_bins")
     return key, count, start, order
+
+
+def mech_bin_noalloc(n, xyz_dev, lo, voxel, dims, key_dev, start_dev, order_dev, stream=None):
+    """Binning into caller-owned device buffers (raw device addresses as ints)
+    with no device allocation by the library: for callers that cannot
+    allocate device memory at the point of the call (see include/mech.h)."""
+    lo = _f64(lo, 3)
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    _check(load_library().mech_bin_noalloc(int(n), ctypes.c_void_p(int(xyz_dev)), _ptr(lo), float(voxel), _ptr(dims),
+                                           ctypes.c_void_p(int(key_dev)), ctypes.c_void_p(int(start_dev)),
+                                           ctypes.c_void_p(int(order_dev)), _stream_handle(stream)),
+           "mech_bin_noalloc")
 
 
 def mech_destroy(h):
