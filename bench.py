@@ -54,9 +54,12 @@ def parse():
     p.add_argument("--workload", default="clustered_20m")
     p.add_argument("--scale", type=float, default=1.0)
     p.add_argument("--mode", default="kahan", choices=["kahan", "mixed", "fp64"])
-    p.add_argument("--voxel", type=float, default=0.0, help="internal voxel side (0: the workload's)")
+    p.add_argument("--voxel", default="min",
+                   help="internal voxel side: a number, 'min' (2 A max R, the smallest valid) or 'user' (the workload's)")
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--graph", type=int, default=0)
+    p.add_argument("--tile", default="4,4,4", help="voxel tile for dense regions, or 0 for none")
+    p.add_argument("--dense-min", type=int, default=16)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -163,10 +166,11 @@ def make_workload(name, scale):
 
 def describe(pop_or_ens, name, args, n, V):
     from paper_2306_11544_gb300 import synth
-    cfg = {"workload": name, "cells": n, "voxels": V, "mode": args.mode, "scale": args.scale}
+    cfg = {"workload": name, "cells": n, "voxels": V, "mode": args.mode, "scale": args.scale,
+           "tile": args.tile, "dense_min": args.dense_min}
     if isinstance(pop_or_ens, synth.Population):
         p = pop_or_ens
-        cfg.update({"voxel_um": p.h if not args.voxel else args.voxel, "dt_min": p.dt, "A": p.A,
+        cfg.update({"voxel_um": p.h, "internal_voxel_um": getattr(args, "voxel_value", p.h), "dt_min": p.dt, "A": p.A,
                     "domain_um": [float(p.lo[0]), float(p.hi[0])]})
         if name == "clustered_20m":
             cfg["layout"] = "16M cells uniform in a 2.5 mm ball + 4M uniform in a 10 mm cube, R 8.41 um"
@@ -260,10 +264,16 @@ def main():
     else:
         m = mech.Mech.from_ensemble(wl, mode=args.mode)
         n = wl.n_total
-    if args.voxel:
-        m.set_internal_voxel(args.voxel)
+    if args.voxel not in ("user", "0"):
+        maxR = max(float(p.R.max()) for p in ([wl] if isinstance(wl, synth.Population) else wl.reps))
+        A = wl.A if isinstance(wl, synth.Population) else wl.reps[0].A
+        vox = 2.0 * A * maxR * (1.0 + 1e-5) if args.voxel == "min" else float(args.voxel)
+        m.set_internal_voxel(vox)
+        args.voxel_value = vox
     if args.block:
         m.set_launch(args.block)
+    tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
+    m.set_tiling(tile, args.dense_min)
     stream = torch.cuda.Stream()
     m.set_stream(stream)
     if args.graph:
@@ -337,10 +347,11 @@ def main():
     peak, peak_kind = hbm_peak()
     roof = None
     if profile and psteps:
-        t_force = phases["force"] / psteps * 1e-3
+        t_force = (phases["classify"] + phases["tiles"] + phases["cells"]) / psteps * 1e-3
         ach = FORCE_BYTES_PER_CELL * n / t_force / 1e9
         tr = force_traffic()
-        roof = {"bound": "hbm", "kernel": "k_force_mixed" if args.mode != "fp64" else "k_force_fp64",
+        kern = "k_force_fp64" if args.mode == "fp64" else "k_tile_classify + k_force_tile + k_force_cells"
+        roof = {"bound": "hbm", "kernel": kern,
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "bytes_per_launch": FORCE_BYTES_PER_CELL * n,

@@ -128,6 +128,16 @@ MECH_API int mech_set_internal_voxel(mech_t* h, double voxel);
  * 32; 0 = default).  Autotuner knob; results do not depend on it. */
 MECH_API int mech_set_launch(mech_t* h, int32_t force_block);
 
+/*
+ * Voxel tiles (autotuner knob): dense regions are processed one tile of
+ * tile_x * tile_y * tile_z voxels at a time, with the tile's halo staged in
+ * shared memory; a tile holding at least dense_min cells is dense.  Supported
+ * tile: 4x4x4 (the default, dense_min 32); (0, 0, 0) sends every cell through
+ * the thread-per-cell kernel.  The FP32 summation order does not depend on
+ * this setting.
+ */
+MECH_API int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t tile_z, int32_t dense_min);
+
 /* Stream (a cudaStream_t) for all device work of this handle; NULL = the
  * handle's own stream.  The caller keeps the stream alive. */
 MECH_API int mech_set_stream(mech_t* h, void* stream);
@@ -154,8 +164,9 @@ MECH_API int mech_compute_velocities(mech_t* h, double* out3n);
  * its phases.  mech_read_profile waits for the stream and returns the summed
  * device milliseconds of each phase since the previous read: phase_ms[0] scan
  * (histogram prefix sum), [1] scatter, [2] in-voxel ordering and FP32 record
- * build, [3] velocity + AB2 (+ next-step histogram), and the number of steps
- * recorded (at most 4096 between reads).
+ * build, [3] tile classification, [4] velocity + AB2 of the cells in dense
+ * tiles, [5] velocity + AB2 of all other cells (all cells in MECH_FP64 mode),
+ * and the number of steps recorded (at most 4096 between reads).
  */
 MECH_API int mech_set_profiling(mech_t* h, int32_t enable);
 MECH_API int mech_read_profile(mech_t* h, double* phase_ms, int64_t* steps);

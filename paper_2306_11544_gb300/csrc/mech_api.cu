@@ -72,6 +72,16 @@ struct mech {
     float2* d_otab_f = nullptr;
     size_t otab_cap = 0;
     size_t grid_cap = 0;
+    // voxel tiles
+    int ltx = 2, lty = 2, ltz = 2;
+    bool use_tiles = true;
+    uint32_t dense_min = 32;
+    uint32_t NT = 0;
+    size_t tcap = 0;
+    uint32_t* d_tcount[2] = {nullptr, nullptr};
+    uint8_t* d_tdense = nullptr;
+    uint32_t* d_tlist = nullptr;
+    uint32_t* d_ndense = nullptr;
     // state
     StateBuf st[2] = {};
     int cur = 0;
@@ -87,6 +97,7 @@ struct mech {
     uint32_t* d_count[2] = {nullptr, nullptr};
     uint32_t* d_start = nullptr;
     uint32_t* d_bsum = nullptr;
+    uint32_t* d_occ = nullptr;
     size_t vcap = 0;  // capacity (entries) of count/start
     double* d_io = nullptr;  // 6n doubles of staging
     float* d_vout_f = nullptr;
@@ -97,6 +108,7 @@ struct mech {
     int64_t step = 0;
     int force_block = 256;
     int force_grid = 0;
+    int tile_grid = 0;
     int elem_grid = 0;
     // graphs: one per starting parity of `cur`
     int graph_steps = 0;
@@ -104,7 +116,7 @@ struct mech {
     size_t dev_bytes = 0;
     std::vector<void*> allocs;
     // per-phase profiling: kProfPhases + 1 events per recorded step
-    static constexpr int kProfPhases = 4;
+    static constexpr int kProfPhases = 6;
     static constexpr int kProfCap = 4096;
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -170,6 +182,7 @@ struct mech {
         a.count_cur = d_count[a_idx];
         a.count_nxt = d_count[a_idx ^ 1];
         a.start = d_start;
+        a.occ = d_occ;
         a.R64 = d_R64;
         a.ccr64 = d_ccr64;
         a.cca64 = d_cca64;
@@ -181,6 +194,18 @@ struct mech {
         a.vout_f = d_vout_f;
         a.vout_d = d_vout_d;
         a.err = d_err;
+        a.ltx = ltx;
+        a.lty = lty;
+        a.ltz = ltz;
+        a.use_tiles = use_tiles ? 1 : 0;
+        a.ntiles = NT;
+        a.dense_min = dense_min;
+        a.tcount_cur = d_tcount[a_idx];
+        a.tcount_nxt = d_tcount[a_idx ^ 1];
+        a.tdense = d_tdense;
+        a.tlist = d_tlist;
+        a.ndense = d_ndense;
+        a.Rmax_f = (float)maxR;
         return a;
     }
 };
@@ -200,7 +225,7 @@ int build_grids(mech_t* h) {
     const double vx = voxel_of(h);
     std::vector<GridDev> g(h->nrep);
     std::vector<double> otd;
-    uint64_t vsum = 0;
+    uint64_t vsum = 0, tsum = 0;
     for (int r = 0; r < h->nrep; ++r) {
         double lo[3], hi[3];
         if (h->dom_auto[r]) {
@@ -228,6 +253,10 @@ int build_grids(mech_t* h) {
         G.cbase = (uint32_t)h->cbase[r];
         G.ncell = (uint32_t)h->counts[r];
         vsum += (uint64_t)G.n[0] * (uint64_t)G.n[1] * (uint64_t)G.n[2];
+        const int lt[3] = {h->ltx, h->lty, h->ltz};
+        for (int d = 0; d < 3; ++d) G.nt[d] = (G.n[d] + (1 << lt[d]) - 1) >> lt[d];
+        G.tbase = (uint32_t)tsum;
+        tsum += (uint64_t)G.nt[0] * (uint64_t)G.nt[1] * (uint64_t)G.nt[2];
         if (vsum > (uint64_t)0x7FFFFFFF - 2 * (uint64_t)kScanTile)
             return fail(MECH_E_OOM, "voxel grids exceed 2^31 voxels; enlarge the voxel or shrink the domain");
     }
@@ -238,15 +267,34 @@ int build_grids(mech_t* h) {
         for (int p = 0; p < 2; ++p) h->free_ptr(h->d_count[p], h->vcap * 4);
         h->free_ptr(h->d_start, h->vcap * 4);
         h->free_ptr(h->d_bsum, h->vcap / kScanTile * 4);
+        h->free_ptr(h->d_occ, (h->vcap / 32 + 1) * 4);
         h->d_count[0] = h->d_count[1] = nullptr;
         h->d_start = nullptr;
         h->d_bsum = nullptr;
+        h->d_occ = nullptr;
         h->vcap = 0;
         MECH_TRY(h->alloc(&h->d_count[0], Vpad));
         MECH_TRY(h->alloc(&h->d_count[1], Vpad));
         MECH_TRY(h->alloc(&h->d_start, Vpad));
         MECH_TRY(h->alloc(&h->d_bsum, Vpad / kScanTile));
+        MECH_TRY(h->alloc(&h->d_occ, Vpad / 32 + 1));
         h->vcap = Vpad;
+    }
+    const uint32_t NT = (uint32_t)tsum;
+    if ((size_t)NT + 1 > h->tcap) {
+        for (int p = 0; p < 2; ++p) h->free_ptr(h->d_tcount[p], h->tcap * 4);
+        h->free_ptr(h->d_tdense, h->tcap);
+        h->free_ptr(h->d_tlist, h->tcap * 4);
+        h->d_tcount[0] = h->d_tcount[1] = nullptr;
+        h->d_tdense = nullptr;
+        h->d_tlist = nullptr;
+        h->tcap = 0;
+        const size_t cap = (size_t)NT + 1;
+        MECH_TRY(h->alloc(&h->d_tcount[0], cap));
+        MECH_TRY(h->alloc(&h->d_tcount[1], cap));
+        MECH_TRY(h->alloc(&h->d_tdense, cap));
+        MECH_TRY(h->alloc(&h->d_tlist, cap));
+        h->tcap = cap;
     }
     if ((size_t)h->nrep > h->grid_cap) {
         h->free_ptr(h->d_grids, h->grid_cap * sizeof(GridDev));
@@ -273,8 +321,12 @@ int build_grids(mech_t* h) {
     CUDA_TRY(cudaMemcpyAsync(h->d_otab_f, otf.data(), otf.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[0], Vpad, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[1], Vpad, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_occ, Vpad / 32 + 1, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_tcount[0], NT, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_tcount[1], NT, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));  // host vectors die here
     h->grids = g;
+    h->NT = NT;
     h->V = V;
     h->Vpad = (uint32_t)Vpad;
     h->grid_dirty = false;
@@ -294,6 +346,7 @@ int ensure_keys(mech_t* h) {
     if (h->keys_valid) return MECH_OK;
     StepArgs a = h->args(h->cur, 1);
     CUDA_TRY(launch_zero_u32(h->d_count[h->cur], h->Vpad, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_tcount[h->cur], h->NT, h->stream));
     CUDA_TRY(launch_keys(a, h->elem_grid, h->stream));
     h->keys_valid = true;
     return MECH_OK;
@@ -305,15 +358,19 @@ int enqueue_step(mech_t* h, int integrate, bool profile = false) {
     cudaEvent_t* ev = nullptr;
     if (profile && h->prof_steps < mech::kProfCap) ev = &h->prof_ev[(size_t)h->prof_steps * (mech::kProfPhases + 1)];
     if (ev) CUDA_TRY(cudaEventRecord(ev[0], h->stream));
-    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, a.count_nxt, h->stream));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, a.count_nxt, h->d_ndense, h->d_occ, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[1], h->stream));
     CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[2], h->stream));
     CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[3], h->stream));
-    CUDA_TRY(launch_force(a, h->force_grid, h->force_block, h->stream));
+    CUDA_TRY(launch_tile_classify(a, h->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[4], h->stream));
+    CUDA_TRY(launch_force_tiles(a, h->tile_grid, h->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[5], h->stream));
+    CUDA_TRY(launch_force_cells(a, h->force_grid, h->force_block, h->stream));
     if (ev) {
-        CUDA_TRY(cudaEventRecord(ev[4], h->stream));
+        CUDA_TRY(cudaEventRecord(ev[6], h->stream));
         ++h->prof_steps;
     }
     h->cur ^= 1;
@@ -346,6 +403,8 @@ int check_err_flag(mech_t* h) {
     if (e) {
         cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
         cudaStreamSynchronize(h->stream);
+        if (e & kErrTimeout)
+            return fail(MECH_E_TIMEOUT, "a bounded wait in the tile kernel gave up (TMA copy did not complete)");
         return fail(MECH_E_DEVICE_FLAG, std::string("device error flag raised: ") +
                                             ((e & kErrNonFinite) ? "non-finite position or velocity " : "") +
                                             ((e & kErrIndex) ? "index out of range" : ""));
@@ -417,8 +476,8 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
         if (rc == MECH_OK) rc = h->alloc(&b.vp64, 3 * np);
         if (rc == MECH_OK) rc = h->alloc(&b.vpf, 3 * np);
         if (rc == MECH_OK) rc = h->alloc(&b.id, np);
-        if (rc == MECH_OK) rc = h->alloc(&b.cand, np);
-        if (rc == MECH_OK) rc = h->alloc(&b.candp, np);
+        if (rc == MECH_OK) rc = h->alloc(&b.recp, np);
+        if (rc == MECH_OK) rc = h->alloc(&b.recq, np);
     }
     if (rc == MECH_OK) rc = h->alloc(&h->d_R64, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_ccr64, np);
@@ -432,16 +491,16 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (rc == MECH_OK) rc = h->alloc(&h->d_vout_f, 3 * np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_vout_d, 3 * np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_err, 1);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_ndense, 1);
     if (rc != MECH_OK) return bail(rc);
 
     // caller order = initial state order; parameters and ids
     std::vector<uint32_t> ids(n);
-    std::vector<float4> cand(n);
-    std::vector<float2> candp(n);
+    std::vector<float4> recp(n), recq(n);
     for (int64_t i = 0; i < n; ++i) {
         ids[i] = (uint32_t)i;
-        cand[i] = make_float4(0.f, 0.f, 0.f, (float)R[i]);
-        candp[i] = make_float2((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]));
+        recp[i] = make_float4(0.f, 0.f, 0.f, (float)R[i]);
+        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), 0.f, 0.f);
     }
     cudaStream_t s = h->stream;
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -449,13 +508,14 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     };
     cudaError_t ce = cudaSuccess;
     if (ce == cudaSuccess) ce = up(h->st[0].id, ids.data(), n * 4);
-    if (ce == cudaSuccess) ce = up(h->st[0].cand, cand.data(), n * sizeof(float4));
-    if (ce == cudaSuccess) ce = up(h->st[0].candp, candp.data(), n * sizeof(float2));
+    if (ce == cudaSuccess) ce = up(h->st[0].recp, recp.data(), n * sizeof(float4));
+    if (ce == cudaSuccess) ce = up(h->st[0].recq, recq.data(), n * sizeof(float4));
     if (ce == cudaSuccess) ce = up(h->d_R64, R, n * 8);
     if (ce == cudaSuccess) ce = up(h->d_ccr64, ccr, n * 8);
     if (ce == cudaSuccess) ce = up(h->d_cca64, cca, n * 8);
     if (ce == cudaSuccess) ce = up(h->d_io, xyz, 3 * n * 8);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(h->d_err, 0, 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(h->d_ndense, 0, 4, s);
     if (ce != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("upload: ") + cudaGetErrorString(ce)));
     StepArgs a = h->args(0, 1);
     ce = launch_load_pos(a, h->st[0], h->d_io, 0, nullptr, s);
@@ -464,6 +524,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (ce != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("initial load: ") + cudaGetErrorString(ce)));
     h->elem_grid = h->sms * 8;
     h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
+    h->tile_grid = tile_kernel_grid(h->args(0, 1), h->sms);
     *out = h;
     return MECH_OK;
 }
@@ -563,6 +624,30 @@ int mech_set_launch(mech_t* h, int32_t force_block) {
     h->force_block = force_block;
     h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
     h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t tile_z, int32_t dense_min) {
+    MECH_TRY(check_handle(h));
+    if (tile_x == 0 && tile_y == 0 && tile_z == 0) {
+        h->use_tiles = false;
+    } else {
+        auto lg = [](int32_t v) { return v == 4 ? 2 : (v == 8 ? 3 : -1); };
+        const int lx = lg(tile_x), ly = lg(tile_y), lz = lg(tile_z);
+        if (!tile_shape_supported(lx, ly, lz))
+            return fail(MECH_E_ARG, "supported tile: 4x4x4 voxels (or 0,0,0 to disable)");
+        if (dense_min < 1) return fail(MECH_E_ARG, "dense_min must be >= 1");
+        h->use_tiles = true;
+        if (lx != h->ltx || ly != h->lty || lz != h->ltz) {
+            h->ltx = lx;
+            h->lty = ly;
+            h->ltz = lz;
+            h->grid_dirty = true;
+        }
+        h->dense_min = (uint32_t)dense_min;
+    }
+    h->invalidate_graphs();
+    if (h->params_set && h->grid_dirty) return build_grids(h);
     return MECH_OK;
 }
 
@@ -777,7 +862,7 @@ int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, 
     h->keys_valid = false;
     MECH_TRY(ensure_keys(h));
     StepArgs a = h->args(h->cur, 1);
-    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, h->stream));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, nullptr, h->d_occ, h->stream));
     CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
     CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
     const size_t n = (size_t)h->n;
@@ -808,7 +893,7 @@ int mech_info(mech_t* h, mech_info_t* out) {
         for (int d = 0; d < 3; ++d) out->dims[d] = h->grids[0].n[d];
     out->voxel = voxel_of(h);
     out->step = h->step;
-    out->launches_per_step = h->n > 0 ? 6 : 0;
+    out->launches_per_step = h->n > 0 ? ((h->mode != kFP64 && h->use_tiles) ? 8 : 7) : 0;
     out->graph_steps = h->graph_steps;
     out->device_bytes = (int64_t)h->dev_bytes;
     return MECH_OK;

@@ -29,12 +29,16 @@ __global__ void k_keys(const StepArgs a) {
     for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
         const uint32_t i = base + lane;
         const bool valid = i < a.n;
-        uint32_t key = 0;
+        uint32_t key = 0, tile = 0;
         if (valid) {
             const int r = rep_of_cell(a.grids, a.nrep, i);
-            key = cell_key(a.mode, a.grids[r], a.A, a.npad, i);
+            const GridDev& g = a.grids[r];
+            int ix, iy, iz;
+            key = cell_key(a.mode, g, a.A, a.npad, i, ix, iy, iz);
+            tile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
         const uint32_t slot = warp_count(a.count_cur, key, valid);
+        warp_add(a.tcount_cur, tile, valid);
         if (valid) {
             a.key[i] = key;
             a.slot[i] = slot;
@@ -88,9 +92,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// One block scans the block sums in place (exclusive).
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, uint32_t nb) {
+// One block scans the block sums in place (exclusive); it also clears one
+// counter word for a later kernel of the same step (may be null).
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, uint32_t nb,
+                                                   uint32_t* __restrict__ zero_word) {
     __shared__ uint32_t sh[33];
+    if (zero_word && threadIdx.x == 0) *zero_word = 0u;
     uint32_t carry = 0;
     for (uint32_t base = 0; base < nb; base += blockDim.x) {
         uint32_t i = base + threadIdx.x;
@@ -107,7 +114,8 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ count,
                                                             const uint32_t* __restrict__ boff,
                                                             uint32_t* __restrict__ start,
-                                                            uint32_t* __restrict__ zero_next) {
+                                                            uint32_t* __restrict__ zero_next,
+                                                            uint16_t* __restrict__ occ16) {
     __shared__ uint32_t sh[33];
     const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
     const uint4* c4 = reinterpret_cast<const uint4*>(count + base);
@@ -130,6 +138,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
         o.w = run; run += q[k].w;
         s4[k] = o;
     }
+    if (occ16) {  // occupancy bits of this thread's 16 voxels
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            m |= (uint32_t)(q[k].x != 0) << (4 * k);
+            m |= (uint32_t)(q[k].y != 0) << (4 * k + 1);
+            m |= (uint32_t)(q[k].z != 0) << (4 * k + 2);
+            m |= (uint32_t)(q[k].w != 0) << (4 * k + 3);
+        }
+        occ16[base / kScanItems] = (uint16_t)m;
+    }
     if (zero_next) {
         uint4* z4 = reinterpret_cast<uint4*>(zero_next + base);
 #pragma unroll
@@ -150,8 +169,8 @@ __global__ void k_scatter(const StepArgs a) {
 
 // Step 1d: rank each cell inside its voxel by caller index (ids are unique),
 // giving its final voxel-order position f; record perm[f], the key, and the
-// force-ready FP32 record of the cell (position relative to its own voxel
-// origin, radius, square roots of the coefficients).
+// force record of the cell: FP32 position relative to the origin of its tile
+// block and radius (recp), square roots of the coefficients (recq).
 __global__ void k_canon(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
@@ -172,28 +191,29 @@ __global__ void k_canon(const StepArgs a) {
         const uint32_t rest = local / (uint32_t)g.n[0];
         const uint32_t iy = rest % (uint32_t)g.n[1];
         const uint32_t iz = rest / (uint32_t)g.n[1];
-        const uint32_t ii[3] = {ix, iy, iz};
+        // origin index of the tile block along each axis
+        const uint32_t ob[3] = {(ix >> a.ltx) << a.ltx, (iy >> a.lty) << a.lty, (iz >> a.ltz) << a.ltz};
         float p[3];
         if (a.mode == kMixedKahan) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float xh = a.A.posf[(size_t)d * a.npad + src];
                 const float c = a.A.comp[(size_t)d * a.npad + src];
-                const float2 o = a.otab_f[g.tab[d] + ii[d]];
-                // (x_hi - c) - (o.hi + o.lo): x_hi - o.hi is exact for a cell in
-                // (or near) the voxel; the small terms are added afterwards.
+                const float2 o = a.otab_f[g.tab[d] + ob[d]];
+                // (x_hi - c) - (o.hi + o.lo): x_hi - o.hi is exact (or nearly so)
+                // for a cell in or near its block; the small terms come after.
                 p[d] = __fsub_rn(__fsub_rn(xh, o.x), __fadd_rn(o.y, c));
             }
         } else {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double x = a.A.pos64[(size_t)d * a.npad + src];
-                p[d] = __double2float_rn(__dsub_rn(x, a.otab_d[g.tab[d] + ii[d]]));
+                p[d] = __double2float_rn(__dsub_rn(x, a.otab_d[g.tab[d] + ob[d]]));
             }
         }
-        const float R = reinterpret_cast<const float*>(a.A.cand)[4 * (size_t)src + 3];
-        a.B.cand[f] = make_float4(p[0], p[1], p[2], R);
-        a.B.candp[f] = a.A.candp[src];
+        const float R = reinterpret_cast<const float*>(a.A.recp)[4 * (size_t)src + 3];
+        a.B.recp[f] = make_float4(p[0], p[1], p[2], R);
+        a.B.recq[f] = a.A.recq[src];
     }
 }
 
@@ -291,11 +311,11 @@ cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start, uint32_t* zero_next,
-                        cudaStream_t s) {
+                        uint32_t* zero_word, uint32_t* occ, cudaStream_t s) {
     const uint32_t nb = vpad / kScanTile;
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(count, bsum);
-    k_scan_top<<<1, 1024, 0, s>>>(bsum, nb);
-    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, zero_next);
+    k_scan_top<<<1, 1024, 0, s>>>(bsum, nb, zero_word);
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, zero_next, reinterpret_cast<uint16_t*>(occ));
     return cudaGetLastError();
 }
 

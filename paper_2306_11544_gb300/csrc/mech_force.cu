@@ -1,24 +1,40 @@
 // Neighbour-gather velocity and AB2 integration (steps 2 and 3 of the
 // mechanics update; the paper's "update velocity" region, Sec. 5.4).
 //
-// Work split: one thread per cell, threads in voxel order.  Each voxel thus
-// gets exactly as many threads as it holds cells (empty voxels get none, the
-// GPU form of the paper's non-empty-voxel list), consecutive threads share
-// neighbour voxels (the locality the paper's voxel-ordered loop was after),
-// and a dense core is spread over as many warps as it has cells / 32.
+// Mixed precision modes run three launches per step:
+//   k_tile_classify   flags every voxel tile (TX x TY x TZ voxels) holding at
+//                     least `dense_min` cells and lists the flagged tiles;
+//   k_force_tile      one CTA per dense tile: the rows of the tile's halo
+//                     (one voxel around it) are contiguous runs of the
+//                     voxel-sorted force records, so each row is staged into
+//                     shared memory by one TMA bulk copy; then one thread per
+//                     target cell tests its 27-voxel neighbourhood there;
+//   k_force_cells     one thread per remaining cell (sparse regions), reading
+//                     its neighbours through L1.
+// The split is the GPU form of the paper's load-balance lesson (Sec. 5.4):
+// work follows voxel occupancy, dense regions are computed tile by tile in
+// mesh order (the coarse, cache-friendly grain the paper recommends) and empty
+// voxels cost nothing.
 //
-// For cell i in voxel (ix, iy, iz) the 27 neighbour voxels are visited in
-// lexicographic (dz, dy, dx) order; the three voxels of one (dy, dz) row are
-// contiguous in the sorted arrays.  Candidate positions are FP32 offsets from
-// their own voxel origin, so the pair vector is (p_i - off) - p_j with
-// off = (dx, dy, dz) h: no FP64 arithmetic in the candidate loop.
+// Candidate tests use a conservative cutoff A (R_i + R_max) so that the loop
+// body is ~10 FP32 instructions; candidates that pass are appended to a short
+// per-thread list (in candidate order) and evaluated afterwards with the exact
+// cutoffs, so the expensive pair term never runs divergently inside the scan.
+// Every cell's sum is taken in the same candidate order: (dz, dy) rows in
+// lexicographic order, cells in voxel order inside a row.
+//
+// FP32 positions are relative to the origin of the cell's tile block; the pair
+// vector is (p_i - o) - p_j where o is the block offset (a multiple of the
+// tile size times h) between the two cells' blocks.  No FP64 arithmetic runs
+// in any candidate loop (FP64 is ~1/62 of FP32 throughput on this GPU).
 #include "mech_internal.cuh"
 
 namespace mk {
 
 namespace {
 
-constexpr int kForceBlock = 256;
+constexpr int kCellBlock = 256;
+constexpr uint32_t kSpinLimit = 1u << 22;
 
 struct Cell3 {
     int ix, iy, iz;
@@ -34,115 +50,512 @@ __device__ __forceinline__ Cell3 decode(uint32_t k, const GridDev& g) {
     return c;
 }
 
-// ---------------------------------------------------------------- FP32 ----
-// Mixed modes: pair arithmetic and the sum in FP32; positions in FP64
-// (MODE = kMixedFP64Pos) or FP32 + Kahan compensation (MODE = kMixedKahan).
+// ------------------------------------------------------- PTX helpers ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on `bar`.
+// Requires 16-byte aligned addresses and a size that is a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after kSpinLimit tries.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ------------------------------------------------- shared arithmetic ----
+
+// Exact pair term (FP32) for a candidate at offset vector r = x_i - x_j with
+// squared length d2.  Adds (c_r - c_a) r / d to acc if 0 < d < A S.
+__device__ __forceinline__ void pair_term(float rx, float ry, float rz, float d2, float Ri, float Rj, float sccri,
+                                          float sccai, float sccrj, float sccaj, float A, float& ax, float& ay,
+                                          float& az) {
+    const float S = Ri + Rj;
+    const float AS = A * S;
+    if (d2 < AS * AS && d2 > 0.f) {
+        const float rd = rsqrtf(d2);
+        const float d = d2 * rd;
+        const float ta = 1.f - __fdividef(d, AS);
+        float cf = -(sccai * sccaj) * (ta * ta);
+        if (d < S) {
+            const float t = 1.f - __fdividef(d, S);
+            cf += (sccri * sccrj) * (t * t);
+        }
+        const float sc = cf * rd;
+        ax += sc * rx;
+        ay += sc * ry;
+        az += sc * rz;
+    }
+}
+
+// AB2 update of cell q (B order) from its A-order state; writes the B state and
+// returns the next step's voxel key, and its voxel coordinates.
 template <int MODE>
-__global__ void __launch_bounds__(kForceBlock) k_force_mixed(const StepArgs a) {
+__device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, float ax, float ay,
+                                                 float az, int& nix, int& niy, int& niz) {
+    const uint32_t src = a.perm[q];
+    const size_t np = a.npad;
+    const float v[3] = {ax, ay, az};
+    bool finite = true;
+    float xf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float vp = a.A.vpf[d * np + src];
+        const float inc = a.dt_f * (1.5f * v[d] - 0.5f * vp);
+        if (MODE == kMixedFP64Pos) {
+            const double x = a.A.pos64[d * np + src];
+            const double xn = a.integrate ? __dadd_rn(x, (double)inc) : x;
+            a.B.pos64[d * np + q] = xn;
+            xf[d] = __double2float_rn(xn);
+            finite = finite && isfinite(xn);
+        } else {
+            float xh = a.A.posf[d * np + src];
+            float cc = a.A.comp[d * np + src];
+            if (a.integrate) {
+                const float y = __fsub_rn(inc, cc);
+                const float t = __fadd_rn(xh, y);
+                cc = __fsub_rn(__fsub_rn(t, xh), y);
+                xh = t;
+            }
+            a.B.posf[d * np + q] = xh;
+            a.B.comp[d * np + q] = cc;
+            xf[d] = xh;
+            finite = finite && isfinite(xh);
+        }
+        a.B.vpf[d * np + q] = a.integrate ? v[d] : vp;
+        if (!a.integrate) a.vout_f[d * np + q] = v[d];
+        finite = finite && isfinite(v[d]);
+    }
+    a.B.id[q] = a.A.id[src];
+    if (!finite) atomicOr(a.err, kErrNonFinite);
+    nix = axis_index_f32(xf[0], g.lo_f[0], g.inv_h_f, g.n[0]);
+    niy = axis_index_f32(xf[1], g.lo_f[1], g.inv_h_f, g.n[1]);
+    niz = axis_index_f32(xf[2], g.lo_f[2], g.inv_h_f, g.n[2]);
+    return g.vbase + (uint32_t)nix + (uint32_t)g.n[0] * ((uint32_t)niy + (uint32_t)g.n[1] * (uint32_t)niz);
+}
+
+// Velocity of cell q by a direct walk over its 27 neighbour voxels in global
+// memory (L1-cached).  Candidate order: (dz, dy) rows, then voxel order.
+__device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, const float4 pi,
+                                              const float4 qi, float& ax, float& ay, float& az) {
+    const float A = a.A_f;
+    const float h = g.h_f;
+    const float bwx = (float)(1 << a.ltx) * h, bwy = (float)(1 << a.lty) * h, bwz = (float)(1 << a.ltz) * h;
+    const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
+    ax = ay = az = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int jz = c.iz + dz;
+        if (jz < 0 || jz >= g.n[2]) continue;
+        const float oz = pi.z - (float)((jz >> a.ltz) - biz) * bwz;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int jy = c.iy + dy;
+            if (jy < 0 || jy >= g.n[1]) continue;
+            const float oy = pi.y - (float)((jy >> a.lty) - biy) * bwy;
+            const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
+            const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
+            const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
+            // occupancy of the (up to) three voxels of this row segment
+            const uint32_t b0 = row + (uint32_t)jx0, sh = b0 & 31u;
+            uint32_t bits = a.occ[b0 >> 5] >> sh;
+            if (sh > 29u) bits |= a.occ[(b0 >> 5) + 1] << (32u - sh);
+            bits &= (1u << (jx1 - jx0 + 1)) - 1u;
+            if (!bits) continue;
+            for (int jx = jx0; jx <= jx1; ++jx) {
+                if (!((bits >> (jx - jx0)) & 1u)) continue;
+                const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
+                const float ox = pi.x - (float)((jx >> a.ltx) - bix) * bwx;
+                for (uint32_t j = s; j < e; ++j) {
+                    const float4 pj = a.B.recp[j];
+                    const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
+                    const float d2 = rx * rx + ry * ry + rz * rz;
+                    const float S = pi.w + pj.w;
+                    const float AS = A * S;
+                    if (d2 < AS * AS && d2 > 0.f) {
+                        const float4 qj = a.B.recq[j];
+                        pair_term(rx, ry, rz, d2, pi.w, pj.w, qi.x, qi.y, qj.x, qj.y, A, ax, ay, az);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------- thread-per-cell kernel ----
+// Every cell not owned by a dense tile (all cells when tiles are off).
+template <int MODE>
+__global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const float A = a.A_f;
     for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
         const uint32_t q = base + lane;
-        const bool valid = q < a.n;
-        uint32_t nkey = 0;
-        if (valid) {
+        bool work = q < a.n;
+        uint32_t nkey = 0, ntile = 0;
+        if (work) {
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(a.vkey_s[q], g);
-            const float4 pi = a.B.cand[q];
-            const float2 ci = a.B.candp[q];
-            const float h = g.h_f;
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            for (int dz = -1; dz <= 1; ++dz) {
-                const int jz = c.iz + dz;
-                if (jz < 0 || jz >= g.n[2]) continue;
-                const float oz = pi.z - (float)dz * h;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int jy = c.iy + dy;
-                    if (jy < 0 || jy >= g.n[1]) continue;
-                    const float oy = pi.y - (float)dy * h;
-                    const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
-                    const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
-                    const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
-                    uint32_t s = a.start[row + jx0];
-                    for (int jx = jx0; jx <= jx1; ++jx) {
-                        const uint32_t e = a.start[row + jx + 1];
-                        const float ox = pi.x - (float)(jx - c.ix) * h;
-                        for (uint32_t j = s; j < e; ++j) {
-                            const float4 pj = a.B.cand[j];
-                            const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
-                            const float d2 = rx * rx + ry * ry + rz * rz;
-                            const float S = pi.w + pj.w;
-                            const float AS = A * S;
-                            if (d2 < AS * AS && d2 > 0.f) {
-                                const float2 cj = a.B.candp[j];
-                                const float rd = rsqrtf(d2);
-                                const float d = d2 * rd;
-                                const float ta = 1.f - __fdividef(d, AS);
-                                float cf = -(ci.y * cj.y) * (ta * ta);
-                                if (d < S) {
-                                    const float t = 1.f - __fdividef(d, S);
-                                    cf += (ci.x * cj.x) * (t * t);
-                                }
-                                const float sc = cf * rd;
-                                ax += sc * rx;
-                                ay += sc * ry;
-                                az += sc * rz;
-                            }
-                        }
-                        s = e;
-                    }
-                }
+            if (a.use_tiles && a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)]) {
+                work = false;
+            } else {
+                float ax, ay, az;
+                velocity_walk(a, g, c, a.B.recp[q], a.B.recq[q], ax, ay, az);
+                int nix, niy, niz;
+                nkey = ab2_epilogue<MODE>(a, g, q, ax, ay, az, nix, niy, niz);
+                ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
             }
-            // ---- AB2 epilogue: read the A-order state of this cell, write B ----
-            const uint32_t src = a.perm[q];
-            const size_t np = a.npad;
-            const float v[3] = {ax, ay, az};
-            bool finite = true;
-            float xf[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float vp = a.A.vpf[d * np + src];
-                const float inc = a.dt_f * (1.5f * v[d] - 0.5f * vp);
-                if (MODE == kMixedFP64Pos) {
-                    const double x = a.A.pos64[d * np + src];
-                    const double xn = a.integrate ? __dadd_rn(x, (double)inc) : x;
-                    a.B.pos64[d * np + q] = xn;
-                    xf[d] = __double2float_rn(xn);
-                    finite = finite && isfinite(xn);
-                } else {
-                    float xh = a.A.posf[d * np + src];
-                    float cc = a.A.comp[d * np + src];
-                    if (a.integrate) {
-                        const float y = __fsub_rn(inc, cc);
-                        const float t = __fadd_rn(xh, y);
-                        cc = __fsub_rn(__fsub_rn(t, xh), y);
-                        xh = t;
-                    }
-                    a.B.posf[d * np + q] = xh;
-                    a.B.comp[d * np + q] = cc;
-                    xf[d] = xh;
-                    finite = finite && isfinite(xh);
-                }
-                a.B.vpf[d * np + q] = a.integrate ? v[d] : vp;
-                if (!a.integrate) a.vout_f[d * np + q] = v[d];
-                finite = finite && isfinite(v[d]);
-            }
-            a.B.id[q] = a.A.id[src];
-            if (!finite) atomicOr(a.err, kErrNonFinite);
-            const int ix = axis_index_f32(xf[0], g.lo_f[0], g.inv_h_f, g.n[0]);
-            const int iy = axis_index_f32(xf[1], g.lo_f[1], g.inv_h_f, g.n[1]);
-            const int iz = axis_index_f32(xf[2], g.lo_f[2], g.inv_h_f, g.n[2]);
-            nkey = g.vbase + (uint32_t)ix + (uint32_t)g.n[0] * ((uint32_t)iy + (uint32_t)g.n[1] * (uint32_t)iz);
         }
-        // histogram of the next step's binning, fused here
-        const uint32_t slot = warp_count(a.count_nxt, nkey, valid);
-        if (valid) {
+        const uint32_t slot = warp_count(a.count_nxt, nkey, work);
+        warp_add(a.tcount_nxt, ntile, work);
+        if (work) {
             a.key[q] = nkey;
             a.slot[q] = slot;
         }
+    }
+}
+
+// ----------------------------------------------------- tile classify ----
+// Flags dense tiles, lists them, clears the next step's tile histogram.
+__global__ void k_tile_classify(const StepArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32u; base < a.ntiles; base += nwarps * 32u) {
+        const uint32_t t = base + lane;
+        const bool valid = t < a.ntiles;
+        bool dense = false;
+        if (valid) {
+            dense = a.tcount_cur[t] >= a.dense_min;
+            a.tdense[t] = dense ? 1 : 0;
+            a.tcount_nxt[t] = 0u;
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, dense);
+        uint32_t off = 0;
+        if (lane == 0 && m) off = atomicAdd(a.ndense, (uint32_t)__popc(m));
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if (dense) a.tlist[off + __popc(m & lanemask_lt())] = t;
+    }
+}
+
+// --------------------------------------------------------- tile kernel ----
+// One CTA per dense tile of 4 x 4 x 4 voxels, per tile:
+//   1. halo row table: for each (y, z) row of the halo (one voxel around the
+//      tile), the global start of its run of force records and the voxel
+//      boundaries inside it;
+//   2. TMA: one bulk copy per row and array (positions, coefficients) into
+//      shared memory, completion on an mbarrier (bounded wait);
+//   3. the staged positions of halo cells that belong to neighbouring tile
+//      blocks are shifted into this tile's block frame, once per cell;
+//   4. for every core voxel, the shared-memory indices of its 27-voxel
+//      neighbourhood (9 contiguous row ranges) are written into one list;
+//   5. one thread per target cell scans its voxel's list: conservative cutoff
+//      test, passing candidates deferred to a per-thread list, exact pair terms
+//      from that list in candidate order; then AB2 and the next-step histogram.
+// A tile whose halo or lists do not fit clears its dense flag and leaves its
+// cells to the thread-per-cell kernel, which runs after this one.
+
+// Exclusive scan of v[0..n) in place by one warp (n small); returns the total.
+__device__ __forceinline__ uint32_t warp_scan_inplace(uint32_t* v, int n) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t carry = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + (int)lane;
+        const uint32_t x = i < n ? v[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if ((int)lane >= o) inc += y;
+        }
+        if (i < n) v[i] = carry + inc - x;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    return carry;
+}
+
+constexpr int kTT = 160;          // threads per tile CTA (about one target each)
+constexpr int kTCap = 768;        // staged halo records per tile
+constexpr int kTListCap = 5120;   // candidate-list entries per tile
+constexpr int kTDefer = 16;       // deferred candidates per thread before a flush
+constexpr size_t kTileDynSmem = (size_t)kTCap * 2 * sizeof(float4) + (size_t)kTListCap * 2 + (size_t)kTT * kTDefer * 2;
+
+template <int MODE>
+__global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
+    constexpr int LT = 2, T4 = 4, HX = T4 + 2, NROW = HX * HX, NVOX = T4 * T4 * T4;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float4* sp = reinterpret_cast<float4*>(dsm);          // positions + radius (tile frame after step 3)
+    float4* sq = sp + kTCap;                              // coefficient square roots
+    uint16_t* clist = reinterpret_cast<uint16_t*>(sq + kTCap);   // per-voxel candidate lists
+    // deferred candidates: entry k of thread t at [k * kTT + t] (no bank conflicts)
+    uint16_t* defer = clist + kTListCap + threadIdx.x;
+    __shared__ uint32_t s_row_gs[NROW];
+    __shared__ uint32_t s_row_off[NROW + 1];
+    __shared__ uint32_t s_row_vb[NROW][HX + 1];
+    __shared__ uint32_t s_vox_loff[NVOX + 1];   // list offset of each core voxel
+    __shared__ uint32_t s_vox_toff[NVOX + 1];   // first target number of each core voxel
+    __shared__ uint16_t s_vp_off[NVOX][9];      // offset of each neighbour row inside a voxel's list
+    __shared__ int s_flag;                       // TMA timeout
+    __shared__ __align__(8) uint64_t s_bar;
+
+    const int tid = threadIdx.x;
+    const uint32_t lane = tid & 31u;
+    const int warp = tid >> 5;
+    const float A = a.A_f;
+    if (tid == 0) {
+        s_flag = 0;
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint32_t ndense = *a.ndense;
+    for (uint32_t it = blockIdx.x; it < ndense; it += gridDim.x) {
+        const uint32_t tile = a.tlist[it];
+        const int r = rep_of_tile(a.grids, a.nrep, tile);
+        const GridDev& g = a.grids[r];
+        const uint32_t lt = tile - g.tbase;
+        const int bx = (int)(lt % (uint32_t)g.nt[0]);
+        const uint32_t rest = lt / (uint32_t)g.nt[0];
+        const int by = (int)(rest % (uint32_t)g.nt[1]);
+        const int bz = (int)(rest / (uint32_t)g.nt[1]);
+        const int x_lo = max(bx * T4 - 1, 0), x_hi = min(bx * T4 + T4, g.n[0] - 1);
+        const int y_lo = max(by * T4 - 1, 0), y_hi = min(by * T4 + T4, g.n[1] - 1);
+        const int z_lo = max(bz * T4 - 1, 0), z_hi = min(bz * T4 + T4, g.n[2] - 1);
+        const int nrx = x_hi - x_lo + 1, nry = y_hi - y_lo + 1, nrz = z_hi - z_lo + 1;
+        const int nrows = nry * nrz;
+        const int kx0 = bx * T4 - x_lo;
+        const int ncx = min(T4, g.n[0] - bx * T4), ncy = min(T4, g.n[1] - by * T4), ncz = min(T4, g.n[2] - bz * T4);
+        const int nvox = ncx * ncy * ncz;
+        // 1. halo row table, one (row, boundary) pair per thread
+        for (int w = tid; w < nrows * (nrx + 1); w += kTT) {
+            const int rr = w / (nrx + 1), k = w - rr * (nrx + 1);
+            const int yy = y_lo + rr % nry, zz = z_lo + rr / nry;
+            const uint32_t rowv = g.vbase + (uint32_t)g.n[0] * ((uint32_t)yy + (uint32_t)g.n[1] * (uint32_t)zz);
+            s_row_vb[rr][k] = a.start[rowv + x_lo + k];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int rr = (int)lane; rr < nrows; rr += 32) {
+                const uint32_t gs = s_row_vb[rr][0];
+                s_row_gs[rr] = gs;
+                s_row_off[rr] = s_row_vb[rr][nrx] - gs;  // row length, scanned below
+            }
+            __syncwarp();
+            const uint32_t total = warp_scan_inplace(s_row_off, nrows);
+            if (lane == 0) s_row_off[nrows] = total;
+        }
+        __syncthreads();
+        for (int w = tid; w < nrows * (nrx + 1); w += kTT) {
+            const int rr = w / (nrx + 1), k = w - rr * (nrx + 1);
+            s_row_vb[rr][k] -= s_row_gs[rr];  // boundaries relative to the row start
+        }
+        const uint32_t total = s_row_off[nrows];
+        __syncthreads();
+        if (total > (uint32_t)kTCap) {  // does not fit: leave the tile to the thread-per-cell kernel
+            if (tid == 0) a.tdense[tile] = 0;
+            continue;
+        }
+        // 2. TMA bulk copies of the halo rows
+        if (warp == 0) {
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4));
+            }
+            __syncwarp();
+            for (int rr = (int)lane; rr < nrows; rr += 32) {
+                const uint32_t len = s_row_vb[rr][nrx];
+                if (len) {
+                    bulk_g2s(&sp[s_row_off[rr]], &a.B.recp[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
+                    bulk_g2s(&sq[s_row_off[rr]], &a.B.recq[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
+                }
+            }
+        }
+        // 4a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
+        if (tid < nvox) {
+            const int v = tid;
+            const int kx = kx0 + v % ncx;
+            const int yy = by * T4 + (v / ncx) % ncy, zz = bz * T4 + v / (ncx * ncy);
+            const int ka = max(kx - 1, 0), kb = min(kx + 1, nrx - 1);
+            uint32_t len = 0;
+            int p = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy, ++p) {
+                    const int z2 = zz + dz, y2 = yy + dy;
+                    s_vp_off[v][p] = (uint16_t)len;
+                    if (z2 < z_lo || z2 > z_hi || y2 < y_lo || y2 > y_hi) continue;
+                    const int r2 = (y2 - y_lo) + nry * (z2 - z_lo);
+                    len += s_row_vb[r2][kb + 1] - s_row_vb[r2][ka];
+                }
+            const int rr = (yy - y_lo) + nry * (zz - z_lo);
+            s_vox_loff[v] = len;
+            s_vox_toff[v] = s_row_vb[rr][kx + 1] - s_row_vb[rr][kx];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t l_total = warp_scan_inplace(s_vox_loff, nvox);
+            const uint32_t t_total = warp_scan_inplace(s_vox_toff, nvox);
+            if (lane == 0) {
+                s_vox_loff[nvox] = l_total;
+                s_vox_toff[nvox] = t_total;
+            }
+        }
+        // 3. wait for the halo
+        if (!mbar_wait_bounded(&s_bar, phase)) s_flag = 1;
+        phase ^= 1u;
+        __syncthreads();
+        if (s_flag) {
+            if (tid == 0) atomicOr(a.err, kErrTimeout);
+            mbar_wait_bounded(&s_bar, phase ^ 1u);  // let copies in flight land first
+            return;
+        }
+        if (s_vox_loff[nvox] > (uint32_t)kTListCap) {  // lists do not fit: same hand-back
+            if (tid == 0) a.tdense[tile] = 0;
+            __syncthreads();
+            continue;
+        }
+        const float bwx = (float)T4 * g.h_f, bwy = bwx, bwz = bwx;
+        // 3b. shift halo cells of neighbouring blocks into this block's frame
+        {
+            const bool left = kx0 == 1;                       // row starts in block bx-1
+            const bool right = x_hi >= bx * T4 + T4;           // row ends in block bx+1
+            for (uint32_t k = tid; k < total; k += kTT) {
+                int lo = 0, hi = nrows - 1;  // row of staged record k
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_row_off[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                const int rr = lo;
+                const uint32_t li = k - s_row_off[rr];
+                const int dbx = (left && li < s_row_vb[rr][1]) ? -1 : ((right && li >= s_row_vb[rr][nrx - 1]) ? 1 : 0);
+                const int dby = ((y_lo + rr % nry) >> LT) - by;
+                const int dbz = ((z_lo + rr / nry) >> LT) - bz;
+                if (dbx | dby | dbz) {
+                    float4 p = sp[k];
+                    p.x += (float)dbx * bwx;
+                    p.y += (float)dby * bwy;
+                    p.z += (float)dbz * bwz;
+                    sp[k] = p;
+                }
+            }
+        }
+        // 4b. candidate index lists, one (voxel, neighbour row) pair per thread
+        for (int w = tid; w < nvox * 9; w += kTT) {
+            const int v = w / 9, p = w - v * 9;
+            const int dz = p / 3 - 1, dy = p % 3 - 1;
+            const int kx = kx0 + v % ncx;
+            const int y2 = by * T4 + (v / ncx) % ncy + dy, z2 = bz * T4 + v / (ncx * ncy) + dz;
+            if (z2 < z_lo || z2 > z_hi || y2 < y_lo || y2 > y_hi) continue;
+            const int ka = max(kx - 1, 0), kb = min(kx + 1, nrx - 1);
+            const int r2 = (y2 - y_lo) + nry * (z2 - z_lo);
+            uint32_t o = s_vox_loff[v] + s_vp_off[v][p];
+            const uint32_t j1 = s_row_off[r2] + s_row_vb[r2][kb + 1];
+            for (uint32_t j = s_row_off[r2] + s_row_vb[r2][ka]; j < j1; ++j) clist[o++] = (uint16_t)j;
+        }
+        __syncthreads();
+        // 5. one thread per target
+        const uint32_t T = s_vox_toff[nvox];
+        for (uint32_t t0 = (uint32_t)warp * 32u; t0 < T; t0 += kTT) {
+            const uint32_t t = t0 + lane;
+            const bool valid = t < T;
+            uint32_t nkey = 0, ntile = 0, q = 0;
+            if (valid) {
+                int v = 0, vhi = nvox - 1;  // core voxel of target t
+                while (v < vhi) {
+                    const int mid = (v + vhi + 1) >> 1;
+                    if (s_vox_toff[mid] <= t) v = mid; else vhi = mid - 1;
+                }
+                const uint32_t k = t - s_vox_toff[v];
+                const int kx = kx0 + v % ncx;
+                const int rr = (by * T4 + (v / ncx) % ncy - y_lo) + nry * (bz * T4 + v / (ncx * ncy) - z_lo);
+                q = s_row_gs[rr] + s_row_vb[rr][kx] + k;
+                const uint32_t si = s_row_off[rr] + s_row_vb[rr][kx] + k;
+                const float4 pi = sp[si];
+                const float4 qi = sq[si];
+                const float cut = A * (pi.w + a.Rmax_f);
+                const float cut2 = cut * cut * 1.0001f;
+                float ax = 0.f, ay = 0.f, az = 0.f;
+                int cnt = 0;
+                const uint32_t l1 = s_vox_loff[v + 1];
+#pragma unroll 4
+                for (uint32_t l = s_vox_loff[v]; l < l1; ++l) {
+                    const uint32_t j = clist[l];
+                    const float4 pj = sp[j];
+                    const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+                    const float d2 = rx * rx + ry * ry + rz * rz;
+                    if (d2 < cut2) {
+                        defer[cnt * kTT] = (uint16_t)j;
+                        if (++cnt == kTDefer) {
+                            for (int m = 0; m < cnt; ++m) {
+                                const uint32_t jj = defer[m * kTT];
+                                const float4 p2 = sp[jj];
+                                const float4 q2 = sq[jj];
+                                const float sx = pi.x - p2.x, sy = pi.y - p2.y, sz = pi.z - p2.z;
+                                pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, pi.w, p2.w, qi.x, qi.y, q2.x, q2.y,
+                                          A, ax, ay, az);
+                            }
+                            cnt = 0;
+                        }
+                    }
+                }
+                for (int m = 0; m < cnt; ++m) {
+                    const uint32_t jj = defer[m * kTT];
+                    const float4 p2 = sp[jj];
+                    const float4 q2 = sq[jj];
+                    const float sx = pi.x - p2.x, sy = pi.y - p2.y, sz = pi.z - p2.z;
+                    pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, pi.w, p2.w, qi.x, qi.y, q2.x, q2.y, A, ax, ay,
+                              az);
+                }
+                int nix, niy, niz;
+                nkey = ab2_epilogue<MODE>(a, g, q, ax, ay, az, nix, niy, niz);
+                ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
+            }
+            const uint32_t slot = warp_count(a.count_nxt, nkey, valid);
+            warp_add(a.tcount_nxt, ntile, valid);
+            if (valid) {
+                a.key[q] = nkey;
+                a.slot[q] = slot;
+            }
+        }
+        __syncthreads();  // shared tables and records are reused by the next tile
     }
 }
 
@@ -152,7 +565,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_mixed(const StepArgs a) {
 // are evaluated in FP64 from the FP64 positions and parameters with the same
 // operations, in the same order, as the definition (no contraction, IEEE sqrt
 // and division), and summed in the definition's candidate order.
-__global__ void __launch_bounds__(kForceBlock) k_force_fp64(const StepArgs a) {
+__global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -162,36 +575,38 @@ __global__ void __launch_bounds__(kForceBlock) k_force_fp64(const StepArgs a) {
     for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
         const uint32_t q = base + lane;
         const bool valid = q < a.n;
-        uint32_t nkey = 0;
+        uint32_t nkey = 0, ntile = 0;
         if (valid) {
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(a.vkey_s[q], g);
-            const float4 pi = a.B.cand[q];
+            const float4 pi = a.B.recp[q];
             const uint32_t src = a.perm[q];
             const uint32_t idi = a.A.id[src];
             const double xi = a.A.pos64[src], yi = a.A.pos64[np + src], zi = a.A.pos64[2 * np + src];
             const double Ri = a.R64[idi], ccri = a.ccr64[idi], ccai = a.cca64[idi];
             const float h = g.h_f;
+            const float bwx = (float)(1 << a.ltx) * h, bwy = (float)(1 << a.lty) * h, bwz = (float)(1 << a.ltz) * h;
+            const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int dz = -1; dz <= 1; ++dz) {
                 const int jz = c.iz + dz;
                 if (jz < 0 || jz >= g.n[2]) continue;
-                const float oz = pi.z - (float)dz * h;
+                const float oz = pi.z - (float)((jz >> a.ltz) - biz) * bwz;
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int jy = c.iy + dy;
                     if (jy < 0 || jy >= g.n[1]) continue;
-                    const float oy = pi.y - (float)dy * h;
+                    const float oy = pi.y - (float)((jy >> a.lty) - biy) * bwy;
                     const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
                     const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
                     const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
                     uint32_t s = a.start[row + jx0];
                     for (int jx = jx0; jx <= jx1; ++jx) {
                         const uint32_t e = a.start[row + jx + 1];
-                        const float ox = pi.x - (float)(jx - c.ix) * h;
+                        const float ox = pi.x - (float)((jx >> a.ltx) - bix) * bwx;
                         for (uint32_t j = s; j < e; ++j) {
                             if (j == q) continue;
-                            const float4 pj = a.B.cand[j];
+                            const float4 pj = a.B.recp[j];
                             const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
                             const float d2f = rx * rx + ry * ry + rz * rz;
                             const float ASf = A * (pi.w + pj.w);
@@ -248,8 +663,10 @@ __global__ void __launch_bounds__(kForceBlock) k_force_fp64(const StepArgs a) {
             const int iy = axis_index_f64(xn[1], g.lo[1], g.inv_h, g.n[1]);
             const int iz = axis_index_f64(xn[2], g.lo[2], g.inv_h, g.n[2]);
             nkey = g.vbase + (uint32_t)ix + (uint32_t)g.n[0] * ((uint32_t)iy + (uint32_t)g.n[1] * (uint32_t)iz);
+            ntile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
         const uint32_t slot = warp_count(a.count_nxt, nkey, valid);
+        warp_add(a.tcount_nxt, ntile, valid);
         if (valid) {
             a.key[q] = nkey;
             a.slot[q] = slot;
@@ -257,27 +674,66 @@ __global__ void __launch_bounds__(kForceBlock) k_force_fp64(const StepArgs a) {
     }
 }
 
+// ---- tile kernel launch ----
+template <int MODE>
+cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
+    static bool configured = false;
+    auto k = k_force_tile<MODE>;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileDynSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<grid, kTT, kTileDynSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool tile_shape_supported(int ltx, int lty, int ltz) {
+    return ltx == 2 && lty == 2 && ltz == 2;
+}
 
 int force_max_blocks_per_sm(int mode, int block) {
     int nb = 0;
     if (mode == kFP64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_fp64, block, 0);
     else if (mode == kMixedFP64Pos)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed<kMixedFP64Pos>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedFP64Pos>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed<kMixedKahan>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedKahan>, block, 0);
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_force(const StepArgs& a, int grid, int block, cudaStream_t s) {
+int tile_kernel_grid(const StepArgs& a, int sms) {
+    (void)a;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_tile<kMixedKahan>, kTT, kTileDynSmem);
+    return sms * (nb > 0 ? nb : 1);
+}
+
+cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
+    if (a.ntiles == 0) return cudaSuccess;
+    int g = (int)((a.ntiles + 255u) / 256u);
+    if (g > 152 * 16) g = 152 * 16;
+    k_tile_classify<<<g, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
+    if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos>(a, grid, s);
+    return launch_tile_mode<kMixedKahan>(a, grid, s);
+}
+
+cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.mode == kFP64)
         k_force_fp64<<<grid, block, 0, s>>>(a);
     else if (a.mode == kMixedFP64Pos)
-        k_force_mixed<kMixedFP64Pos><<<grid, block, 0, s>>>(a);
+        k_force_cells<kMixedFP64Pos><<<grid, block, 0, s>>>(a);
     else
-        k_force_mixed<kMixedKahan><<<grid, block, 0, s>>>(a);
+        k_force_cells<kMixedKahan><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -10,16 +10,25 @@
 //       vp64   [3][npad] double   previous velocity (FP64 mode)
 //       vpf    [3][npad] float    previous velocity (mixed modes)
 //       id     [n]       u32      caller index of the cell
-//       cand   [n]       float4   {p_x, p_y, p_z, R}: p = position relative to
-//                                 the origin of the cell's own voxel, FP32
-//       candp  [n]       float2   {sqrt(ccr), sqrt(cca)}
+//       recp   [n]       float4   {x, y, z, R}: FP32 position relative to the
+//                                 origin of the cell's tile block (below), radius
+//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), 0, 0}
 //   * binning scratch: key/slot [n] (key and within-voxel arrival slot of
 //     each cell in A order), vkey_s [n] (key in B order), perm [n] (A index of
 //     the cell at each B position), tmp [n] u64 (id << 32 | A index, scattered
 //     by key), count[2][Vpad] (histograms of this and the next step),
 //     start[Vpad] (exclusive scan of count: cells of voxel v are the sorted
-//     positions start[v] .. start[v+1]-1).
+//     positions start[v] .. start[v+1]-1), occ[Vpad/32 + 1] (bit v: count > 0).
+//   * voxel tiles: the grid is cut into blocks of TX x TY x TZ voxels (powers
+//     of two); tcount[2][T] counts the cells of each tile (this step, next
+//     step), tdense[T] flags the tiles processed by the shared-memory tile
+//     kernel and tlist holds their indices (ndense of them).
 //   * per-replicate grid descriptors and per-axis voxel-origin tables.
+//
+// FP32 positions in the force record are relative to the origin of the cell's
+// tile block (voxel index rounded down to a multiple of the tile size), so one
+// row of a tile halo copied verbatim into shared memory needs an offset only
+// where it crosses into a neighbouring block.
 #pragma once
 
 #include <cstdint>
@@ -38,6 +47,9 @@ constexpr int kScanTile = kScanThreads * kScanItems;  // voxels per scan block
 // Device error flag bits (the host reports any of them as MECH_E_DEVICE_FLAG).
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrIndex = 2u;
+constexpr uint32_t kErrTimeout = 4u;
+
+
 
 struct GridDev {
     double lo[3];
@@ -49,6 +61,8 @@ struct GridDev {
     uint32_t cbase;    // first cell (same in caller and voxel order)
     uint32_t ncell;
     uint32_t tab[3];   // offset of each axis in the origin tables
+    int32_t nt[3];     // tiles per axis
+    uint32_t tbase;    // first global tile index of this replicate
 };
 
 struct StateBuf {
@@ -58,8 +72,8 @@ struct StateBuf {
     double* vp64;
     float* vpf;
     uint32_t* id;
-    float4* cand;
-    float2* candp;
+    float4* recp;
+    float4* recq;
 };
 
 struct StepArgs {
@@ -79,6 +93,7 @@ struct StepArgs {
     uint32_t* count_cur;
     uint32_t* count_nxt;
     uint32_t* start;
+    uint32_t* occ;         // 1 bit per voxel: count > 0 (written by the scan)
     const double* R64;    // FP64 parameters in caller order (FP64 mode)
     const double* ccr64;
     const double* cca64;
@@ -88,13 +103,24 @@ struct StepArgs {
     float* vout_f;         // velocities-only output, B order (mixed modes)
     double* vout_d;        // velocities-only output, B order (FP64 mode)
     uint32_t* err;
+    // tiles
+    int ltx, lty, ltz;     // log2 of the tile dimensions (voxels)
+    int use_tiles;         // 1: dense tiles go to the shared-memory tile kernel
+    uint32_t ntiles;       // tiles over all replicates
+    uint32_t dense_min;    // a tile with at least this many cells is dense
+    uint32_t* tcount_cur;
+    uint32_t* tcount_nxt;
+    uint8_t* tdense;
+    uint32_t* tlist;
+    uint32_t* ndense;
+    float Rmax_f;          // largest radius (conservative candidate cutoff)
 };
 
 // ---- launch wrappers (mech_bin.cu) ----
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
 cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start,
-                        uint32_t* zero_next, cudaStream_t s);
+                        uint32_t* zero_next, uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
 cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);
@@ -103,14 +129,21 @@ cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const fl
 cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double* in, int raw_kahan,
                             const double* comp_in, cudaStream_t s);
 cudaError_t launch_load_vprev(const StepArgs& a, const StateBuf& st, const double* in, cudaStream_t s);
-cudaError_t launch_build_cand(const StepArgs& a, const StateBuf& st, cudaStream_t s);
 
 // ---- error reporting of the C ABI (mech_api.cu): sets mech_last_error ----
 int record_error(int code, const std::string& msg);
 
 // ---- launch wrappers (mech_force.cu) ----
-cudaError_t launch_force(const StepArgs& a, int grid, int block, cudaStream_t s);
+// Velocity + AB2 of every cell: FP64 kernel, or (mixed modes) the tile
+// classification, the shared-memory tile kernel for dense tiles and the
+// thread-per-cell kernel for the rest.  Each phase is a separate launch so
+// that it can be timed; `ev` (may be null) receives an event between phases.
+cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStream_t s);
 int force_max_blocks_per_sm(int mode, int block);
+int tile_kernel_grid(const StepArgs& a, int sms);
+bool tile_shape_supported(int ltx, int lty, int ltz);
 
 // ---- small device helpers shared by the kernel files ----
 __device__ __forceinline__ int rep_of_cell(const GridDev* g, int nrep, uint32_t q) {
@@ -147,10 +180,24 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+__device__ __forceinline__ int rep_of_tile(const GridDev* g, int nrep, uint32_t t) {
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g[mid].tbase <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t tile_index(const GridDev& g, int ix, int iy, int iz, int ltx, int lty,
+                                               int ltz) {
+    return g.tbase + (uint32_t)(ix >> ltx) +
+           (uint32_t)g.nt[0] * ((uint32_t)(iy >> lty) + (uint32_t)g.nt[1] * (uint32_t)(iz >> ltz));
+}
+
 // Voxel key of the cell at state index i (positions in state buffer st).
 __device__ __forceinline__ uint32_t cell_key(int mode, const GridDev& g, const StateBuf& st, uint32_t npad,
-                                             uint32_t i) {
-    int ix, iy, iz;
+                                             uint32_t i, int& ix, int& iy, int& iz) {
     if (mode == kFP64) {
         ix = axis_index_f64(st.pos64[i], g.lo[0], g.inv_h, g.n[0]);
         iy = axis_index_f64(st.pos64[npad + i], g.lo[1], g.inv_h, g.n[1]);
@@ -178,6 +225,14 @@ __device__ __forceinline__ uint32_t warp_count(uint32_t* count, uint32_t key, bo
     if (valid && lane == leader) base = atomicAdd(&count[key], (uint32_t)__popc(grp));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
     return base + (uint32_t)__popc(grp & lanemask_lt());
+}
+
+// Warp-aggregated increment without a slot (tile histogram).
+__device__ __forceinline__ void warp_add(uint32_t* count, uint32_t key, bool valid) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t k = valid ? key : 0xFFFFFFFFu;
+    uint32_t grp = __match_any_sync(0xFFFFFFFFu, k);
+    if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(&count[key], (uint32_t)__popc(grp));
 }
 
 }  // namespace mk

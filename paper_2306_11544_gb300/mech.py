@@ -40,7 +40,7 @@ MODES = {"fp64": MECH_FP64, "mixed": MECH_MIXED_FP64POS, "fp64pos": MECH_MIXED_F
 EXPORTS = [
     "mech_last_error", "mech_version", "mech_create", "mech_create_batch", "mech_set_params",
     "mech_set_domain", "mech_set_precision", "mech_set_internal_voxel", "mech_set_launch",
-    "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
+    "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
     "mech_load_state", "mech_debug_bins", "mech_bin_noalloc", "mech_info", "mech_grid", "mech_destroy",
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
             "mech_set_precision": ([_P, ctypes.c_int], ctypes.c_int),
             "mech_set_internal_voxel": ([_P, ctypes.c_double], ctypes.c_int),
             "mech_set_launch": ([_P, ctypes.c_int32], ctypes.c_int),
+            "mech_set_tiling": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
             "mech_set_stream": ([_P, _P], ctypes.c_int),
             "mech_set_graph": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_step": ([_P, ctypes.c_int64], ctypes.c_int),
@@ -196,6 +197,11 @@ def mech_set_launch(h, force_block):
     _check(load_library().mech_set_launch(h, int(force_block)), "mech_set_launch")
 
 
+def mech_set_tiling(h, tile=(4, 4, 4), dense_min=32):
+    tx, ty, tz = (0, 0, 0) if tile is None else tile
+    _check(load_library().mech_set_tiling(h, int(tx), int(ty), int(tz), int(dense_min)), "mech_set_tiling")
+
+
 def mech_set_stream(h, stream):
     _check(load_library().mech_set_stream(h, _stream_handle(stream)), "mech_set_stream")
 
@@ -212,12 +218,12 @@ def mech_set_profiling(h, enable):
     _check(load_library().mech_set_profiling(h, int(bool(enable))), "mech_set_profiling")
 
 
-PHASES = ("scan", "scatter", "canon", "force")
+PHASES = ("scan", "scatter", "canon", "classify", "tiles", "cells")
 
 
 def mech_read_profile(h):
     """Summed device ms per phase since the last read, and the step count."""
-    ms = np.zeros(4)
+    ms = np.zeros(len(PHASES))
     steps = ctypes.c_int64()
     _check(load_library().mech_read_profile(h, _ptr(ms), ctypes.byref(steps)), "mech_read_profile")
     return dict(zip(PHASES, ms.tolist())), int(steps.value)
@@ -362,6 +368,9 @@ class Mech:
 
     def set_launch(self, block):
         mech_set_launch(self.h, block)
+
+    def set_tiling(self, tile=(4, 4, 4), dense_min=32):
+        mech_set_tiling(self.h, tile, dense_min)
 
     def set_stream(self, stream):
         mech_set_stream(self.h, stream)

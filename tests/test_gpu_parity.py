@@ -227,3 +227,49 @@ def test_nonfinite_state_raises_device_flag():
         with pytest.raises(mech.MechError) as e:
             m.sync()
         assert e.value.code == mech.MECH_E_DEVICE_FLAG
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+@pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1)],
+                         ids=["cells_only", "t444", "t444_all_dense"])
+def test_tiled_force_matches_oracle(mode, tiling):
+    """The shared-memory tile kernel (dense tiles) and the thread-per-cell
+    kernel (the rest) give the same velocities as the oracle, for every tile
+    shape and density threshold, including every tile treated as dense."""
+    pop = synth.clustered_20m(seed=9, scale=0.002)
+    with H.make(pop, mode) as m:
+        m.set_tiling(*tiling) if tiling else m.set_tiling(None)
+        for _ in range(2):
+            x = m.positions()
+            m.step(1)
+            v = m.velocities()
+            vref = oracle.velocities(x, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+            assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+        check_bins(m, pop, mode)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_tile_halo_overflow_falls_back(mode):
+    """A crowd whose tile halo exceeds the shared-memory capacity is handed
+    back to the thread-per-cell kernel."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    xyz = rng.uniform(0.0, 55.0, size=(3000, 3))
+    pop = H.tiny_population(xyz, [0] * 3, [240] * 3)
+    with H.make(pop, mode) as m:
+        m.set_tiling((4, 4, 4), 32)
+        v = m.compute_velocities()
+    vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+
+
+def test_internal_voxel_with_tiles_over_steps():
+    """Autotuner-style setting: minimum internal voxel, 4x4x4 tiles, Kahan,
+    20 steps against the FP64 oracle trajectory."""
+    pop = synth.clustered_20m(seed=10, scale=0.001)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    with H.make(pop, "kahan", voxel=hmin) as m:
+        m.set_tiling((4, 4, 4), 32)
+        m.step(20)
+        x = m.positions()
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, 20)
+    assert np.abs(x - xr).max() <= H.TOL_X_MIXED
