@@ -64,6 +64,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--autotune", action="store_true", help="pick voxel/tile/block with the autotuner first")
+    p.add_argument("--precision-study", action="store_true",
+                   help="long-horizon study: batched Kahan and FP64-position runs of the 32-replicate ensemble "
+                        "against an FP64 run of its smallest replicate; prints one JSON line")
+    p.add_argument("--plain-loop", action="store_true",
+                   help="ensembles: also time the plain single-population path looped over replicates")
     return p.parse_args()
 
 
@@ -236,10 +242,93 @@ def cpu_baseline(pop):
             "sample": f"one full oracle step (bin+force+AB2, FP64) of all {n} cells, {t:.1f} s"}
 
 
+def time_plain_loop(ens, args, stream, torch):
+    """The plain single-population API looped over the replicates: one handle
+    per replicate, each advanced `steps` steps on the same stream."""
+    from paper_2306_11544_gb300 import mech
+    hs = []
+    for p in ens.reps:
+        h = mech.Mech.from_population(p, mode=args.mode)
+        if args.voxel not in ("user", "0"):
+            h.set_internal_voxel(getattr(args, "voxel_value", p.h))
+        tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
+        h.set_tiling(tile, args.dense_min)
+        h.set_stream(stream)
+        hs.append(h)
+    for h in hs:
+        h.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for h in hs:
+        h.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n = sum(p.n for p in ens.reps)
+    launches = sum(h.info()["launches_per_step"] for h in hs)
+    for h in hs:
+        h.close()
+    return {"value": n * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "handles": len(hs), "launches_per_step": launches}
+
+
+def precision_study(args):
+    """Final-position error of the batched mixed modes after the workload's
+    steps, on the smallest replicate, against the FP64 mode (whose every step
+    reproduces the oracle's operations; its first step is checked against the
+    oracle here on all cells of that replicate)."""
+    import torch
+    import oracle
+    from paper_2306_11544_gb300 import build as libbuild
+    from paper_2306_11544_gb300 import mech
+    libbuild.build()
+    oracle.build()
+    ens = make_workload(args.workload if args.workload != "clustered_20m" else "ensemble_32_long", args.scale)
+    steps = args.steps if args.steps != 200 else ens.steps
+    small = min(range(len(ens.reps)), key=lambda r: ens.reps[r].n)
+    p0 = ens.reps[small]
+    off = sum(p.n for p in ens.reps[:small])
+    out = {"metric": "final-position max error vs FP64, smallest replicate", "workload": ens.name,
+           "replicates": len(ens.reps), "cells": ens.n_total, "steps": steps, "smallest_replicate_cells": p0.n}
+    stream = torch.cuda.Stream()
+    with mech.Mech.from_population(p0, mode="fp64") as ref:
+        v0 = ref.compute_velocities()
+        vr = oracle.velocities(p0.xyz, p0.R, p0.ccr, p0.cca, p0.A, p0.lo, p0.h, oracle.grid_dims(p0.lo, p0.hi, p0.h))
+        out["fp64_first_step_bit_identical_to_oracle"] = bool(np.array_equal(v0, vr))
+        ref.set_stream(stream)
+        t0 = time.perf_counter()
+        ref.step(steps)
+        ref.sync()
+        out["fp64_reference_s"] = time.perf_counter() - t0
+        xref = ref.positions()
+    for mode in ("kahan", "mixed"):
+        with mech.Mech.from_ensemble(ens, mode=mode) as m:
+            maxR = max(float(p.R.max()) for p in ens.reps)
+            m.set_internal_voxel(2.0 * ens.reps[0].A * maxR * (1.0 + 1e-5))
+            m.set_tiling((4, 4, 4), 16)
+            m.set_stream(stream)
+            m.set_graph(100 if steps % 100 == 0 else 0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            m.step(steps)
+            ev1.record(stream)
+            ev1.synchronize()
+            m.sync()
+            ms = ev0.elapsed_time(ev1)
+            x = m.positions()[off:off + p0.n]
+        out[mode] = {"max_abs_err_um": float(np.abs(x - xref).max()), "ms_per_step": ms / steps,
+                     "cell_steps_per_s": ens.n_total * steps / (ms * 1e-3)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return precision_study(args)
     ws, rank, local = dist_env()
     import torch
     from paper_2306_11544_gb300 import build as libbuild
@@ -258,12 +347,15 @@ def main():
     mech.load_library()
 
     wl = make_workload(args.workload, args.scale)
-    if isinstance(wl, synth.Population):
+    batched = not isinstance(wl, synth.Population)
+    if not batched:
         m = mech.Mech.from_population(wl, mode=args.mode)
         n = wl.n
     else:
         m = mech.Mech.from_ensemble(wl, mode=args.mode)
         n = wl.n_total
+        if not args.graph:
+            args.graph = 100 if args.steps % 100 == 0 else 2 * max(1, args.steps // 20)
     if args.voxel not in ("user", "0"):
         maxR = max(float(p.R.max()) for p in ([wl] if isinstance(wl, synth.Population) else wl.reps))
         A = wl.A if isinstance(wl, synth.Population) else wl.reps[0].A
@@ -274,6 +366,13 @@ def main():
         m.set_launch(args.block)
     tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
     m.set_tiling(tile, args.dense_min)
+    tuned = None
+    if args.autotune:
+        from paper_2306_11544_gb300 import autotune
+        reps = [wl] if not batched else wl.reps
+        maxR = max(float(p.R.max()) for p in reps)
+        tuned = autotune.autotune(m, 2.0 * reps[0].A * maxR * (1.0 + 1e-5), reps[0].h, cache_path=None)
+        args.voxel_value = tuned["best"]["voxel"]
     stream = torch.cuda.Stream()
     m.set_stream(stream)
     if args.graph:
@@ -286,6 +385,7 @@ def main():
     m.sync()
 
     # timed region: K steps, events on the library's stream, phase events inside
+    # (graphs replay without phase events; their phases come from a separate pass)
     profile = not args.graph
     if profile:
         m.set_profiling(True)
@@ -312,6 +412,17 @@ def main():
         pg.barrier()
     total_cells = n * ws
     value = total_cells * args.steps / (t_max * 1e-3)
+    if not profile:  # graph run: phases from a short profiled pass after the timed region
+        m.set_profiling(True)
+        m.step(max(2, min(20, args.steps)))
+        phases, psteps = m.read_profile()
+        m.set_profiling(False)
+        profile = True
+
+    plain = None
+    if batched and args.plain_loop:
+        plain = time_plain_loop(wl, args, stream, torch)
+        plain["batched_over_plain"] = value / plain["value"]
 
     # end to end through the C ABI: pinned host positions in, step, positions out
     e2e = None
@@ -375,6 +486,14 @@ def main():
         "e2e": e2e,
         "gpu_launches": info["launches_per_step"] * args.steps,
     }
+    if batched:
+        line["batched"] = {"replicates": len(wl.reps), "graph_steps": args.graph,
+                           "launches_per_step": info["launches_per_step"]}
+        if plain is not None:
+            line["plain_looped"] = plain
+    if tuned is not None:
+        line["autotune"] = {"best": tuned["best"], "trials": [
+            {k: t[k] for k in ("voxel", "tile", "dense_min", "block", "ms_per_step")} for t in tuned["trials"]]}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

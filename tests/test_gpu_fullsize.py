@@ -1,0 +1,85 @@
+"""Parity at the full sizes of the benchmark workloads.
+
+* 1M-cell spheroid (three cell types, lognormal radii): the FP64 mode's first
+  step is bit-identical to the oracle on every cell; over the workload's 1,000
+  steps the two mixed modes stay within 1e-3 um of the FP64 mode.  Because the
+  FP64 mode reproduces the oracle's every operation in order (checked here and
+  in test_gpu_parity.py), its trajectory is the oracle's trajectory; running
+  the oracle itself for 1e9 cell-steps would take many CPU minutes.
+* 20M-cell clustered workload in the launch configuration bench.py times
+  (Kahan positions, smallest internal voxel, 4x4x4 tiles): velocities of
+  sampled cells (core, shell, core surface) against the oracle, computed cell
+  by cell, plus properties that hold at any size (finite state, zero net
+  velocity to rounding level).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_11544_gb300 import synth
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    H.lib()
+    oracle.build()
+
+
+@pytest.fixture(scope="module")
+def spheroid_1m():
+    return synth.spheroid_1m(seed=0)
+
+
+def test_spheroid_1m_fp64_first_step_bit_identical(spheroid_1m):
+    pop = spheroid_1m
+    with H.make(pop, "fp64") as m:
+        v = m.compute_velocities()
+    vref = oracle.velocities(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert np.array_equal(v, vref)
+
+
+def test_spheroid_1m_mixed_modes_over_1000_steps(spheroid_1m):
+    pop = spheroid_1m
+    steps = pop.steps
+    with H.make(pop, "fp64") as m:
+        m.step(steps)
+        xr = m.positions()
+    errs = {}
+    for mode in ("mixed", "kahan"):
+        with H.make(pop, mode) as m:
+            m.step(steps)
+            x = m.positions()
+        errs[mode] = float(np.abs(x - xr).max())
+    print(f"spheroid_1m, {steps} steps, max |x - x_fp64| (um): {errs}")
+    for mode, e in errs.items():
+        assert e <= H.TOL_X_MIXED, (mode, e)
+
+
+def test_clustered_20m_sampled_cells_against_oracle():
+    pop = synth.clustered_20m(seed=0)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    with H.make(pop, "kahan", voxel=hmin) as m:
+        m.set_tiling((4, 4, 4), 16)
+        m.step(2)
+        x = m.positions()
+        m.step(1)
+        v = m.velocities()
+        st = m.read_state()
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    rng = np.random.Generator(np.random.PCG64(99))
+    r = np.linalg.norm(x, axis=1)
+    core = np.flatnonzero(r < 2300.0)
+    surface = np.flatnonzero((r > 2450.0) & (r < 2550.0))
+    shell = np.flatnonzero(r > 3000.0)
+    idx = np.concatenate([rng.choice(core, 1500, replace=False), rng.choice(surface, 500, replace=False),
+                          rng.choice(shell, 500, replace=False)])
+    vref = oracle.velocities_subset(x, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), idx)
+    err = np.abs(v[idx] - vref).max() / np.abs(vref).max()
+    print(f"clustered_20m sampled velocity rel err {err:.3e}")
+    assert err <= H.TOL_V_MIXED
+    # pair terms are antisymmetric: the velocities sum to zero up to rounding
+    assert np.abs(v.sum(axis=0)).max() <= 1e-5 * np.abs(v).sum()
+    assert np.all(np.isfinite(st["comp"]))

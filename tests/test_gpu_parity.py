@@ -273,3 +273,65 @@ def test_internal_voxel_with_tiles_over_steps():
         x = m.positions()
     xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, 20)
     assert np.abs(x - xr).max() <= H.TOL_X_MIXED
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batched_equals_plain_per_replicate(mode):
+    """Replicates advanced together in one batched handle (graph replay) give,
+    replicate by replicate, exactly the positions of separate handles."""
+    from paper_2306_11544_gb300 import mech
+    ens = synth.ensemble_256(seed=5, scale=0.05, n_rep=6)
+    with mech.Mech.from_ensemble(ens, mode=mode) as b:
+        b.set_graph(4)
+        b.step(9)
+        xb = b.positions()
+        vb = b.velocities()
+    off = 0
+    for p in ens.reps:
+        with H.make(p, mode) as m:
+            m.step(9)
+            x = m.positions()
+            v = m.velocities()
+        assert np.array_equal(xb[off:off + p.n], x), p.name
+        assert np.array_equal(vb[off:off + p.n], v), p.name
+        off += p.n
+
+
+def test_batch_with_empty_and_tiny_replicates():
+    from paper_2306_11544_gb300 import mech
+    a = H.tiny_population([[0.0, 0.0, 0.0], [15.0, 0.0, 0.0]], [-60] * 3, [60] * 3)
+    b = H.tiny_population(np.zeros((0, 3)), [-60] * 3, [60] * 3)
+    c = synth.spheroid_2k(seed=12, n=300)
+    xyz = np.concatenate([a.xyz, b.xyz, c.xyz])
+    cat = lambda f: np.concatenate([getattr(a, f), getattr(b, f), getattr(c, f)])
+    with mech.Mech(xyz, cat("R"), cat("ccr"), cat("cca"), counts=[a.n, b.n, c.n]) as m:
+        m.set_params(1.25, 30.0, 0.1)
+        for r, p in enumerate((a, b, c)):
+            m.set_domain(r, p.lo, p.hi)
+        m.set_precision("fp64")
+        v = m.compute_velocities()
+    va = oracle.velocities(a.xyz, a.R, a.ccr, a.cca, 1.25, a.lo, 30.0, H.dims_of(a))
+    vc = oracle.velocities(c.xyz, c.R, c.ccr, c.cca, 1.25, c.lo, 30.0, H.dims_of(c))
+    assert np.array_equal(v, np.concatenate([va, vc]))
+
+
+def test_autotuner_restores_state_and_stays_correct():
+    from paper_2306_11544_gb300 import autotune
+    pop = synth.clustered_20m(seed=13, scale=0.002)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    cfgs = [{"voxel": hmin, "tile": (4, 4, 4), "dense_min": 16, "block": 128},
+            {"voxel": pop.h, "tile": None, "dense_min": 0, "block": 256}]
+    with H.make(pop, "kahan") as m:
+        m.step(2)
+        before = m.read_state()
+        res = autotune.autotune(m, hmin, pop.h, steps=2, warmup=1, cache_path=None, configs=cfgs)
+        after = m.read_state()
+        for k in ("xyz", "vprev", "comp"):
+            assert np.array_equal(before[k], after[k]), k
+        assert res["best"] in cfgs and len(res["trials"]) == 4
+        assert m.info()["voxel"] == pytest.approx(res["best"]["voxel"])
+        x = m.positions()
+        m.step(1)
+        v = m.velocities()
+    vref = oracle.velocities(x, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert H.rel_err(v, vref) <= H.TOL_V_MIXED
