@@ -236,6 +236,22 @@ MECH_API int mech_bin_noalloc(int64_t n, const double* xyz, const double lo[3], 
                               const int32_t dims[3], uint32_t* key, uint32_t* start, uint32_t* order,
                               void* stream);
 
+/*
+ * Fault injection for tests of the failure paths (host-armed; nothing here
+ * makes a GPU fault, trap or hang).  MECH_FAULT_TILE_WAIT: the tile kernel's
+ * copy barrier expects 16 bytes more than are copied, so its wait can never
+ * complete; the wait gives up after 1 ms, the kernel sets its error flag and
+ * returns, and the next synchronising call reports MECH_E_TIMEOUT.
+ * MECH_FAULT_ALLOC (h may be NULL): the next device allocation by any handle
+ * fails with MECH_E_OOM.  MECH_FAULT_NONE disarms both.  After any device
+ * error the handle refuses mech_step and mech_write_positions (MECH_E_STATE)
+ * until the whole state is reloaded with mech_load_state.
+ */
+#define MECH_FAULT_NONE 0
+#define MECH_FAULT_TILE_WAIT 1
+#define MECH_FAULT_ALLOC 2
+MECH_API int mech_debug_inject(mech_t* h, int32_t fault);
+
 typedef struct {
     int64_t n_cells;
     int32_t n_rep;

@@ -6,6 +6,7 @@
 // management inside the hot loop).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -19,6 +20,7 @@ using namespace mk;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<int> g_fault_alloc{0};  // host-armed: the next device allocation fails
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -107,6 +109,8 @@ struct mech {
     bool keys_valid = false;
     int64_t step = 0;
     int force_block = 256;
+    uint32_t fault = 0;            // host-armed fault injection (kFault* bits)
+    bool poisoned = false;         // a device error left the state inconsistent
     int force_grid = 0;
     int tile_grid = 0;
     int elem_grid = 0;
@@ -135,6 +139,9 @@ struct mech {
         *p = nullptr;
         size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
         void* q = nullptr;
+        int armed = 1;
+        if (g_fault_alloc.compare_exchange_strong(armed, 0))
+            return fail(MECH_E_OOM, "injected allocation failure (mech_debug_inject)");
         cudaError_t e = cudaMalloc(&q, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -144,6 +151,9 @@ struct mech {
         allocs.push_back(q);
         dev_bytes += bytes;
         *p = static_cast<T*>(q);
+        // scratch starts at zero: indices read from it are always in range
+        if (cudaMemset(q, 0, bytes) != cudaSuccess)
+            return fail(MECH_E_CUDA, "cudaMemset of a new buffer failed");
         return MECH_OK;
     }
 
@@ -206,6 +216,8 @@ struct mech {
         a.tlist = d_tlist;
         a.ndense = d_ndense;
         a.Rmax_f = (float)maxR;
+        a.fault = fault;
+        a.wait_ns = (fault & kFaultTileWait) ? 1000000ull : 2000000000ull;  // 1 ms armed, 2 s otherwise
         return a;
     }
 };
@@ -255,6 +267,17 @@ int build_grids(mech_t* h) {
         vsum += (uint64_t)G.n[0] * (uint64_t)G.n[1] * (uint64_t)G.n[2];
         const int lt[3] = {h->ltx, h->lty, h->ltz};
         for (int d = 0; d < 3; ++d) G.nt[d] = (G.n[d] + (1 << lt[d]) - 1) >> lt[d];
+        // hi grid: every value within (tile + 2 halo voxels) x 1.5 of reach stays below 2^23 q
+        const double reach = 1.5 * (double)((1 << std::max(h->ltx, std::max(h->lty, h->ltz))) + 2) * vx;
+        const int k = (int)std::floor(23.0 - std::log2(reach));
+        G.q = (float)std::ldexp(1.0, -k);
+        G.inv_q = (float)std::ldexp(1.0, k);
+        for (int d = 0; d < 3; ++d) {
+            const double w = (double)(1 << lt[d]) * vx;
+            const double wq = std::nearbyint(w / (double)G.q) * (double)G.q;
+            G.bwq[d] = (float)wq;
+            G.bwl[d] = (float)(w - wq);
+        }
         G.tbase = (uint32_t)tsum;
         tsum += (uint64_t)G.nt[0] * (uint64_t)G.nt[1] * (uint64_t)G.nt[2];
         if (vsum > (uint64_t)0x7FFFFFFF - 2 * (uint64_t)kScanTile)
@@ -403,6 +426,7 @@ int check_err_flag(mech_t* h) {
     if (e) {
         cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
         cudaStreamSynchronize(h->stream);
+        h->poisoned = true;
         if (e & kErrTimeout)
             return fail(MECH_E_TIMEOUT, "a bounded wait in the tile kernel gave up (TMA copy did not complete)");
         return fail(MECH_E_DEVICE_FLAG, std::string("device error flag raised: ") +
@@ -499,8 +523,8 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     std::vector<float4> recp(n), recq(n);
     for (int64_t i = 0; i < n; ++i) {
         ids[i] = (uint32_t)i;
-        recp[i] = make_float4(0.f, 0.f, 0.f, (float)R[i]);
-        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), 0.f, 0.f);
+        recp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), (float)R[i], 0.f);
     }
     cudaStream_t s = h->stream;
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -688,6 +712,8 @@ int mech_set_precision(mech_t* h, int mode) {
 
 int mech_step(mech_t* h, int64_t n_steps) {
     MECH_TRY(ready(h));
+    if (h->poisoned)
+        return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
     if (n_steps < 0) return fail(MECH_E_ARG, "negative step count");
     if (n_steps == 0 || h->n == 0) {
         h->step += n_steps;
@@ -792,6 +818,8 @@ int mech_write_positions(mech_t* h, const double* xyz3n) {
     MECH_TRY(check_handle(h));
     if (h->n == 0) return MECH_OK;
     if (!xyz3n) return fail(MECH_E_ARG, "null input");
+    if (h->poisoned)
+        return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
     CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz3n, 3 * (size_t)h->n * 8, cudaMemcpyHostToDevice, h->stream));
     StepArgs a = h->args(h->cur, 1);
     CUDA_TRY(launch_load_pos(a, h->st[h->cur], h->d_io, 0, nullptr, h->stream));
@@ -849,6 +877,7 @@ int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const dou
     h->step = step;
     h->keys_valid = false;
     h->vout_valid = false;
+    h->poisoned = false;
     return MECH_OK;
 }
 
@@ -878,6 +907,22 @@ int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, 
     if (order)
         for (size_t f = 0; f < n; ++f) order[f] = ids[perm[f]];
     return check_err_flag(h);
+}
+
+int mech_debug_inject(mech_t* h, int32_t fault) {
+    if (fault == MECH_FAULT_ALLOC) {
+        g_fault_alloc.store(1);
+        return MECH_OK;
+    }
+    if (fault == MECH_FAULT_NONE) {
+        g_fault_alloc.store(0);
+        if (!h) return MECH_OK;
+    }
+    MECH_TRY(check_handle(h));
+    if (fault != MECH_FAULT_NONE && fault != MECH_FAULT_TILE_WAIT) return fail(MECH_E_ARG, "unknown fault");
+    h->fault = fault == MECH_FAULT_TILE_WAIT ? kFaultTileWait : 0u;
+    h->invalidate_graphs();
+    return MECH_OK;
 }
 
 int mech_info(mech_t* h, mech_info_t* out) {

@@ -163,27 +163,42 @@ __global__ void k_scatter(const StepArgs a) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const uint32_t k = a.key[i];
         const uint32_t dst = a.start[k] + a.slot[i];
+        if (dst >= a.n) {  // only after an earlier device error left the keys inconsistent
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
         a.tmp[dst] = ((unsigned long long)a.A.id[i] << 32) | (unsigned long long)i;
     }
 }
 
 // Step 1d: rank each cell inside its voxel by caller index (ids are unique),
 // giving its final voxel-order position f; record perm[f], the key, and the
-// force record of the cell: FP32 position relative to the origin of its tile
-// block and radius (recp), square roots of the coefficients (recq).
+// force record of the cell: its position relative to the origin of its tile
+// block split into a hi part on the power-of-two grid q and a residual lo
+// (recp = {hi.x, hi.y, hi.z, lo.z}), and the square roots of the coefficients,
+// the radius and lo.x, lo.y as a half2 in units of q (recq).
 __global__ void k_canon(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const unsigned long long e = a.tmp[q];
         const uint32_t id = (uint32_t)(e >> 32);
         const uint32_t src = (uint32_t)e;
+        if (src >= a.n) {  // only after an earlier device error
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
         const uint32_t k = a.key[src];
         const uint32_t s = a.start[k], en = a.start[k + 1];
         uint32_t rank = 0;
         for (uint32_t t = s; t < en; ++t) rank += (uint32_t)((uint32_t)(a.tmp[t] >> 32) < id);
         const uint32_t f = s + rank;
+        if (f >= a.n) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
         a.perm[f] = src;
         a.vkey_s[f] = k;
+        a.B.id[f] = id;  // written here, so the next state's slot map is complete even if a force kernel aborts
         const int r = rep_of_cell(a.grids, a.nrep, f);
         const GridDev& g = a.grids[r];
         const uint32_t local = k - g.vbase;
@@ -193,27 +208,33 @@ __global__ void k_canon(const StepArgs a) {
         const uint32_t iz = rest / (uint32_t)g.n[1];
         // origin index of the tile block along each axis
         const uint32_t ob[3] = {(ix >> a.ltx) << a.ltx, (iy >> a.lty) << a.lty, (iz >> a.ltz) << a.ltz};
-        float p[3];
+        // position relative to the block origin as hi (on the q grid) + lo
+        float hi[3], lo[3];
         if (a.mode == kMixedKahan) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float xh = a.A.posf[(size_t)d * a.npad + src];
                 const float c = a.A.comp[(size_t)d * a.npad + src];
                 const float2 o = a.otab_f[g.tab[d] + ob[d]];
-                // (x_hi - c) - (o.hi + o.lo): x_hi - o.hi is exact (or nearly so)
-                // for a cell in or near its block; the small terms come after.
-                p[d] = __fsub_rn(__fsub_rn(xh, o.x), __fadd_rn(o.y, c));
+                // value = (x_hi - o.hi) - (o.lo + c), both sums error-free
+                float e1, e2;
+                const float s1 = two_sum(xh, -o.x, e1);
+                const float s = two_sum(s1, -__fadd_rn(o.y, c), e2);
+                hi[d] = quantize_hi(s, g.q, g.inv_q);
+                lo[d] = __fadd_rn(__fsub_rn(s, hi[d]), __fadd_rn(e1, e2));
             }
         } else {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double x = a.A.pos64[(size_t)d * a.npad + src];
-                p[d] = __double2float_rn(__dsub_rn(x, a.otab_d[g.tab[d] + ob[d]]));
+                const double r = __dsub_rn(x, a.otab_d[g.tab[d] + ob[d]]);
+                hi[d] = quantize_hi(__double2float_rn(r), g.q, g.inv_q);
+                lo[d] = __double2float_rn(__dsub_rn(r, (double)hi[d]));
             }
         }
-        const float R = reinterpret_cast<const float*>(a.A.recp)[4 * (size_t)src + 3];
-        a.B.recp[f] = make_float4(p[0], p[1], p[2], R);
-        a.B.recq[f] = a.A.recq[src];
+        const float4 qo = a.A.recq[src];
+        a.B.recp[f] = make_float4(hi[0], hi[1], hi[2], lo[2]);
+        a.B.recq[f] = make_float4(qo.x, qo.y, qo.z, pack_lo_xy(lo[0], lo[1], g.inv_q));
     }
 }
 

@@ -17,15 +17,16 @@
 // voxels cost nothing.
 //
 // Candidate tests use a conservative cutoff A (R_i + R_max) so that the loop
-// body is ~10 FP32 instructions; candidates that pass are appended to a short
-// per-thread list (in candidate order) and evaluated afterwards with the exact
-// cutoffs, so the expensive pair term never runs divergently inside the scan.
+// body is ~10 FP32 instructions; in the tile kernel the tests of 32 candidates
+// set bits of a hit mask and only the hits are then evaluated with the exact
+// cutoffs, so the expensive pair term never runs inside the scan.
 // Every cell's sum is taken in the same candidate order: (dz, dy) rows in
 // lexicographic order, cells in voxel order inside a row.
 //
-// FP32 positions are relative to the origin of the cell's tile block; the pair
-// vector is (p_i - o) - p_j where o is the block offset (a multiple of the
-// tile size times h) between the two cells' blocks.  No FP64 arithmetic runs
+// FP32 positions are relative to the origin of the cell's tile block, stored as
+// a hi part on a power-of-two grid plus a residual lo; the pair vector is
+// (hi_i - hi_j - o_hi) + (lo_i - lo_j - o_lo), o the block offset between the
+// two cells' blocks, exact up to its final rounding.  No FP64 arithmetic runs
 // in any candidate loop (FP64 is ~1/62 of FP32 throughput on this GPU).
 #include "mech_internal.cuh"
 
@@ -34,7 +35,7 @@ namespace mk {
 namespace {
 
 constexpr int kCellBlock = 256;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 26;
 
 struct Cell3 {
     int ix, iy, iz;
@@ -95,10 +96,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier, giving up after kSpinLimit tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier; give up after `limit_ns` of wall
+// time (or kSpinLimit tries, whichever comes first).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 
@@ -165,7 +176,6 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
         if (!a.integrate) a.vout_f[d * np + q] = v[d];
         finite = finite && isfinite(v[d]);
     }
-    a.B.id[q] = a.A.id[src];
     if (!finite) atomicOr(a.err, kErrNonFinite);
     nix = axis_index_f32(xf[0], g.lo_f[0], g.inv_h_f, g.n[0]);
     niy = axis_index_f32(xf[1], g.lo_f[1], g.inv_h_f, g.n[1]);
@@ -174,45 +184,57 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
 }
 
 // Velocity of cell q by a direct walk over its 27 neighbour voxels in global
-// memory (L1-cached).  Candidate order: (dz, dy) rows, then voxel order.
+// memory (L1-cached).  Candidate order: (dz, dy) rows, then voxel order.  The
+// occupancy bits of all nine rows are fetched first (independent loads), so
+// a cell with few or no neighbours costs one round of memory latency, not nine.
+// Candidates are tested on the hi parts with the conservative cutoff; a pair
+// that passes is evaluated from hi + lo.
 __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, const float4 pi,
                                               const float4 qi, float& ax, float& ay, float& az) {
     const float A = a.A_f;
-    const float h = g.h_f;
-    const float bwx = (float)(1 << a.ltx) * h, bwy = (float)(1 << a.lty) * h, bwz = (float)(1 << a.ltz) * h;
     const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
-    ax = ay = az = 0.f;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int jz = c.iz + dz;
-        if (jz < 0 || jz >= g.n[2]) continue;
-        const float oz = pi.z - (float)((jz >> a.ltz) - biz) * bwz;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int jy = c.iy + dy;
-            if (jy < 0 || jy >= g.n[1]) continue;
-            const float oy = pi.y - (float)((jy >> a.lty) - biy) * bwy;
+    const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
+    const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
+    const uint32_t wmask = (1u << (jx1 - jx0 + 1)) - 1u;
+    uint32_t occ9 = 0u;  // 3 occupancy bits per (dz, dy) row, row p at bits 3p..3p+2
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int jz = c.iz + p / 3 - 1, jy = c.iy + p % 3 - 1;
+        if (jz >= 0 && jz < g.n[2] && jy >= 0 && jy < g.n[1]) {
             const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
-            const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
-            const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
-            // occupancy of the (up to) three voxels of this row segment
             const uint32_t b0 = row + (uint32_t)jx0, sh = b0 & 31u;
-            uint32_t bits = a.occ[b0 >> 5] >> sh;
-            if (sh > 29u) bits |= a.occ[(b0 >> 5) + 1] << (32u - sh);
-            bits &= (1u << (jx1 - jx0 + 1)) - 1u;
-            if (!bits) continue;
-            for (int jx = jx0; jx <= jx1; ++jx) {
-                if (!((bits >> (jx - jx0)) & 1u)) continue;
-                const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
-                const float ox = pi.x - (float)((jx >> a.ltx) - bix) * bwx;
-                for (uint32_t j = s; j < e; ++j) {
-                    const float4 pj = a.B.recp[j];
-                    const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
-                    const float d2 = rx * rx + ry * ry + rz * rz;
-                    const float S = pi.w + pj.w;
-                    const float AS = A * S;
-                    if (d2 < AS * AS && d2 > 0.f) {
-                        const float4 qj = a.B.recq[j];
-                        pair_term(rx, ry, rz, d2, pi.w, pj.w, qi.x, qi.y, qj.x, qj.y, A, ax, ay, az);
-                    }
+            uint32_t w = a.occ[b0 >> 5] >> sh;
+            if (sh > 29u) w |= a.occ[(b0 >> 5) + 1] << (32u - sh);
+            occ9 |= (w & wmask) << (3 * p);
+        }
+    }
+    const float2 lxy = unpack_lo_xy(qi.w, g.q);
+    const float cut = A * (qi.z + a.Rmax_f);
+    const float cut2 = cut * cut * 1.0001f;
+    ax = ay = az = 0.f;
+#pragma unroll 1
+    for (int p = 0; p < 9; ++p) {
+        const uint32_t rb = (occ9 >> (3 * p)) & 7u;
+        if (!rb) continue;
+        const int jz = c.iz + p / 3 - 1, jy = c.iy + p % 3 - 1;
+        const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
+        const float dbz = (float)((jz >> a.ltz) - biz), dby = (float)((jy >> a.lty) - biy);
+        const float oz = pi.z - dbz * g.bwq[2], ozl = pi.w - dbz * g.bwl[2];   // exact on the q grid
+        const float oy = pi.y - dby * g.bwq[1], oyl = lxy.y - dby * g.bwl[1];
+        for (int jx = jx0; jx <= jx1; ++jx) {
+            if (!((rb >> (jx - jx0)) & 1u)) continue;
+            const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
+            const float dbx = (float)((jx >> a.ltx) - bix);
+            const float ox = pi.x - dbx * g.bwq[0], oxl = lxy.x - dbx * g.bwl[0];
+            for (uint32_t j = s; j < e; ++j) {
+                const float4 pj = a.B.recp[j];
+                const float hx = ox - pj.x, hy = oy - pj.y, hz = oz - pj.z;
+                if (hx * hx + hy * hy + hz * hz < cut2) {
+                    const float4 qj = a.B.recq[j];
+                    const float2 lj = unpack_lo_xy(qj.w, g.q);
+                    const float rx = hx + (oxl - lj.x), ry = hy + (oyl - lj.y), rz = hz + (ozl - pj.w);
+                    pair_term(rx, ry, rz, rx * rx + ry * ry + rz * rz, qi.z, qj.z, qi.x, qi.y, qj.x, qj.y, A, ax, ay,
+                              az);
                 }
             }
         }
@@ -287,9 +309,10 @@ __global__ void k_tile_classify(const StepArgs a) {
 //      blocks are shifted into this tile's block frame, once per cell;
 //   4. for every core voxel, the shared-memory indices of its 27-voxel
 //      neighbourhood (9 contiguous row ranges) are written into one list;
-//   5. one thread per target cell scans its voxel's list: conservative cutoff
-//      test, passing candidates deferred to a per-thread list, exact pair terms
-//      from that list in candidate order; then AB2 and the next-step histogram.
+//   5. one thread per target cell scans its voxel's list 32 candidates at a
+//      time: a branch-free conservative cutoff test builds a hit mask, then the
+//      exact pair terms of the hits are summed in list order; then AB2 and the
+//      next-step histogram.
 // A tile whose halo or lists do not fit clears its dense flag and leaves its
 // cells to the thread-per-cell kernel, which runs after this one.
 
@@ -315,8 +338,7 @@ __device__ __forceinline__ uint32_t warp_scan_inplace(uint32_t* v, int n) {
 constexpr int kTT = 160;          // threads per tile CTA (about one target each)
 constexpr int kTCap = 768;        // staged halo records per tile
 constexpr int kTListCap = 5120;   // candidate-list entries per tile
-constexpr int kTDefer = 16;       // deferred candidates per thread before a flush
-constexpr size_t kTileDynSmem = (size_t)kTCap * 2 * sizeof(float4) + (size_t)kTListCap * 2 + (size_t)kTT * kTDefer * 2;
+constexpr size_t kTileDynSmem = (size_t)kTCap * 2 * sizeof(float4) + (size_t)kTListCap * 2;
 
 template <int MODE>
 __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
@@ -325,8 +347,6 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
     float4* sp = reinterpret_cast<float4*>(dsm);          // positions + radius (tile frame after step 3)
     float4* sq = sp + kTCap;                              // coefficient square roots
     uint16_t* clist = reinterpret_cast<uint16_t*>(sq + kTCap);   // per-voxel candidate lists
-    // deferred candidates: entry k of thread t at [k * kTT + t] (no bank conflicts)
-    uint16_t* defer = clist + kTListCap + threadIdx.x;
     __shared__ uint32_t s_row_gs[NROW];
     __shared__ uint32_t s_row_off[NROW + 1];
     __shared__ uint32_t s_row_vb[NROW][HX + 1];
@@ -398,7 +418,8 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
         if (warp == 0) {
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4));
+                mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4) +
+                                                  ((a.fault & kFaultTileWait) ? 16u : 0u));
             }
             __syncwarp();
             for (int rr = (int)lane; rr < nrows; rr += 32) {
@@ -439,12 +460,12 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
             }
         }
         // 3. wait for the halo
-        if (!mbar_wait_bounded(&s_bar, phase)) s_flag = 1;
+        if (!mbar_wait_bounded(&s_bar, phase, a.wait_ns)) s_flag = 1;
         phase ^= 1u;
         __syncthreads();
         if (s_flag) {
             if (tid == 0) atomicOr(a.err, kErrTimeout);
-            mbar_wait_bounded(&s_bar, phase ^ 1u);  // let copies in flight land first
+            mbar_wait_bounded(&s_bar, phase ^ 1u, a.wait_ns);  // let copies in flight land first
             return;
         }
         if (s_vox_loff[nvox] > (uint32_t)kTListCap) {  // lists do not fit: same hand-back
@@ -453,27 +474,37 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
             continue;
         }
         const float bwx = (float)T4 * g.h_f, bwy = bwx, bwz = bwx;
-        // 3b. shift halo cells of neighbouring blocks into this block's frame
+        // 3b. shift halo cells of neighbouring blocks into this block's frame,
+        // one warp per halo row: hi by a multiple of the q-grid block width
+        // (exact), the remainder of the width into lo
         {
             const bool left = kx0 == 1;                       // row starts in block bx-1
             const bool right = x_hi >= bx * T4 + T4;           // row ends in block bx+1
-            for (uint32_t k = tid; k < total; k += kTT) {
-                int lo = 0, hi = nrows - 1;  // row of staged record k
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_row_off[mid] <= k) lo = mid; else hi = mid - 1;
-                }
-                const int rr = lo;
-                const uint32_t li = k - s_row_off[rr];
-                const int dbx = (left && li < s_row_vb[rr][1]) ? -1 : ((right && li >= s_row_vb[rr][nrx - 1]) ? 1 : 0);
+            for (int rr = warp; rr < nrows; rr += kTT / 32) {
                 const int dby = ((y_lo + rr % nry) >> LT) - by;
                 const int dbz = ((z_lo + rr / nry) >> LT) - bz;
-                if (dbx | dby | dbz) {
-                    float4 p = sp[k];
-                    p.x += (float)dbx * bwx;
-                    p.y += (float)dby * bwy;
-                    p.z += (float)dbz * bwz;
-                    sp[k] = p;
+                const uint32_t len = s_row_vb[rr][nrx];
+                const uint32_t lend = left ? s_row_vb[rr][1] : 0u;         // [0, lend): block bx-1
+                const uint32_t rbeg = right ? s_row_vb[rr][nrx - 1] : len;  // [rbeg, len): block bx+1
+                if (dby == 0 && dbz == 0 && lend == 0 && rbeg == len) continue;
+                float4* prow = sp + s_row_off[rr];
+                float4* qrow = sq + s_row_off[rr];
+                for (uint32_t li = lane; li < len; li += 32u) {
+                    const int dbx = li < lend ? -1 : (li >= rbeg ? 1 : 0);
+                    if (dbx | dby | dbz) {
+                        float4 p = prow[li];
+                        float4 qq = qrow[li];
+                        float2 l = unpack_lo_xy(qq.w, g.q);
+                        p.x += (float)dbx * g.bwq[0];
+                        p.y += (float)dby * g.bwq[1];
+                        p.z += (float)dbz * g.bwq[2];
+                        p.w += (float)dbz * g.bwl[2];
+                        l.x += (float)dbx * g.bwl[0];
+                        l.y += (float)dby * g.bwl[1];
+                        qq.w = pack_lo_xy(l.x, l.y, g.inv_q);
+                        prow[li] = p;
+                        qrow[li] = qq;
+                    }
                 }
             }
         }
@@ -510,39 +541,37 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
                 const uint32_t si = s_row_off[rr] + s_row_vb[rr][kx] + k;
                 const float4 pi = sp[si];
                 const float4 qi = sq[si];
-                const float cut = A * (pi.w + a.Rmax_f);
+                const float2 li = unpack_lo_xy(qi.w, g.q);
+                const float cut = A * (qi.z + a.Rmax_f);
                 const float cut2 = cut * cut * 1.0001f;
                 float ax = 0.f, ay = 0.f, az = 0.f;
-                int cnt = 0;
-                const uint32_t l1 = s_vox_loff[v + 1];
-#pragma unroll 4
-                for (uint32_t l = s_vox_loff[v]; l < l1; ++l) {
-                    const uint32_t j = clist[l];
-                    const float4 pj = sp[j];
-                    const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
-                    const float d2 = rx * rx + ry * ry + rz * rz;
-                    if (d2 < cut2) {
-                        defer[cnt * kTT] = (uint16_t)j;
-                        if (++cnt == kTDefer) {
-                            for (int m = 0; m < cnt; ++m) {
-                                const uint32_t jj = defer[m * kTT];
-                                const float4 p2 = sp[jj];
-                                const float4 q2 = sq[jj];
-                                const float sx = pi.x - p2.x, sy = pi.y - p2.y, sz = pi.z - p2.z;
-                                pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, pi.w, p2.w, qi.x, qi.y, q2.x, q2.y,
-                                          A, ax, ay, az);
-                            }
-                            cnt = 0;
-                        }
+                // scan the list 32 candidates at a time: a branch-free test on the
+                // hi parts builds a hit mask, then the exact pair terms of the hits
+                // (from hi + lo) are summed in list order
+                const uint32_t l0 = s_vox_loff[v], l1 = s_vox_loff[v + 1];
+                for (uint32_t cb = l0; cb < l1; cb += 32u) {
+                    const uint32_t nc = min(32u, l1 - cb);
+                    uint32_t hits = 0;
+#pragma unroll 8
+                    for (uint32_t k = 0; k < nc; ++k) {
+                        const float4 pj = sp[clist[cb + k]];
+                        const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+                        const float d2 = rx * rx + ry * ry + rz * rz;
+                        hits |= (d2 < cut2 ? 1u : 0u) << k;
                     }
-                }
-                for (int m = 0; m < cnt; ++m) {
-                    const uint32_t jj = defer[m * kTT];
-                    const float4 p2 = sp[jj];
-                    const float4 q2 = sq[jj];
-                    const float sx = pi.x - p2.x, sy = pi.y - p2.y, sz = pi.z - p2.z;
-                    pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, pi.w, p2.w, qi.x, qi.y, q2.x, q2.y, A, ax, ay,
-                              az);
+                    while (hits) {
+                        const uint32_t k = (uint32_t)(__ffs(hits) - 1);
+                        hits &= hits - 1u;
+                        const uint32_t jj = clist[cb + k];
+                        const float4 p2 = sp[jj];
+                        const float4 q2 = sq[jj];
+                        const float2 l2 = unpack_lo_xy(q2.w, g.q);
+                        const float sx = (pi.x - p2.x) + (li.x - l2.x);
+                        const float sy = (pi.y - p2.y) + (li.y - l2.y);
+                        const float sz = (pi.z - p2.z) + (pi.w - p2.w);
+                        pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, qi.z, q2.z, qi.x, qi.y, q2.x, q2.y, A, ax,
+                                  ay, az);
+                    }
                 }
                 int nix, niy, niz;
                 nkey = ab2_epilogue<MODE>(a, g, q, ax, ay, az, nix, niy, niz);
@@ -585,8 +614,8 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
             const uint32_t idi = a.A.id[src];
             const double xi = a.A.pos64[src], yi = a.A.pos64[np + src], zi = a.A.pos64[2 * np + src];
             const double Ri = a.R64[idi], ccri = a.ccr64[idi], ccai = a.cca64[idi];
-            const float h = g.h_f;
-            const float bwx = (float)(1 << a.ltx) * h, bwy = (float)(1 << a.lty) * h, bwz = (float)(1 << a.ltz) * h;
+            const float bwx = g.bwq[0], bwy = g.bwq[1], bwz = g.bwq[2];
+            const float ASf = A * (a.B.recq[q].z + a.Rmax_f);  // conservative: the largest partner radius
             const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int dz = -1; dz <= 1; ++dz) {
@@ -609,7 +638,6 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
                             const float4 pj = a.B.recp[j];
                             const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
                             const float d2f = rx * rx + ry * ry + rz * rz;
-                            const float ASf = A * (pi.w + pj.w);
                             if (!(d2f <= ASf * ASf * 1.0001f + 1e-2f)) continue;
                             const uint32_t sj = a.perm[j];
                             const uint32_t idj = a.A.id[sj];
@@ -657,7 +685,6 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
                 if (!a.integrate) a.vout_d[d * np + q] = v[d];
                 finite = finite && isfinite(xn[d]) && isfinite(v[d]);
             }
-            a.B.id[q] = idi;
             if (!finite) atomicOr(a.err, kErrNonFinite);
             const int ix = axis_index_f64(xn[0], g.lo[0], g.inv_h, g.n[0]);
             const int iy = axis_index_f64(xn[1], g.lo[1], g.inv_h, g.n[1]);

@@ -10,9 +10,11 @@
 //       vp64   [3][npad] double   previous velocity (FP64 mode)
 //       vpf    [3][npad] float    previous velocity (mixed modes)
 //       id     [n]       u32      caller index of the cell
-//       recp   [n]       float4   {x, y, z, R}: FP32 position relative to the
-//                                 origin of the cell's tile block (below), radius
-//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), 0, 0}
+//       recp   [n]       float4   {x_hi, y_hi, z_hi, z_lo}: position relative to
+//                                 the origin of the cell's tile block (below) as
+//                                 a hi part on a fixed power-of-two grid q plus
+//                                 a small residual lo
+//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), R, half2(x_lo/q, y_lo/q)}
 //   * binning scratch: key/slot [n] (key and within-voxel arrival slot of
 //     each cell in A order), vkey_s [n] (key in B order), perm [n] (A index of
 //     the cell at each B position), tmp [n] u64 (id << 32 | A index, scattered
@@ -28,12 +30,18 @@
 // FP32 positions in the force record are relative to the origin of the cell's
 // tile block (voxel index rounded down to a multiple of the tile size), so one
 // row of a tile halo copied verbatim into shared memory needs an offset only
-// where it crosses into a neighbouring block.
+// where it crosses into a neighbouring block.  The hi parts and the block
+// widths lie on a grid of spacing q = 2^-k chosen so that every hi value, block
+// offset and their sums and differences within a tile's reach are exactly
+// representable in FP32; a pair's relative vector is then
+// (hi_i - hi_j - offset_hi) + (lo_i - lo_j - offset_lo), exact up to its final
+// rounding.  Candidate tests use the hi parts only (error <= q).
 #pragma once
 
 #include <cstdint>
 #include <string>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace mk {
@@ -63,7 +71,38 @@ struct GridDev {
     uint32_t tab[3];   // offset of each axis in the origin tables
     int32_t nt[3];     // tiles per axis
     uint32_t tbase;    // first global tile index of this replicate
+    float q, inv_q;    // grid of the hi parts of record positions (a power of two)
+    float bwq[3];      // tile-block width per axis rounded to the q grid
+    float bwl[3];      // the remainder of the block width (FP64 width - bwq)
 };
+
+// Split of a position p (relative to its tile-block origin) into a hi part on
+// the q grid and a residual; lo is stored scaled by 1/q as FP16 for x and y.
+__device__ __forceinline__ float quantize_hi(float p, float q, float inv_q) {
+    const float t = p * inv_q;
+    return fabsf(t) < 8388608.f ? rintf(t) * q : p;
+}
+
+__device__ __forceinline__ float pack_lo_xy(float lx, float ly, float inv_q) {
+    const float sx = fminf(fmaxf(lx * inv_q, -60000.f), 60000.f);
+    const float sy = fminf(fmaxf(ly * inv_q, -60000.f), 60000.f);
+    const __half2 h = __floats2half2_rn(sx, sy);
+    return *reinterpret_cast<const float*>(&h);
+}
+
+__device__ __forceinline__ float2 unpack_lo_xy(float w, float q) {
+    const __half2 h = *reinterpret_cast<const __half2*>(&w);
+    const float2 f = __half22float2(h);
+    return make_float2(f.x * q, f.y * q);
+}
+
+// Error-free sum: s + e == a + b exactly (Knuth).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
 
 struct StateBuf {
     double* pos64;
@@ -114,7 +153,12 @@ struct StepArgs {
     uint32_t* tlist;
     uint32_t* ndense;
     float Rmax_f;          // largest radius (conservative candidate cutoff)
+    unsigned long long wait_ns;  // time limit of every device-side wait
+    uint32_t fault;        // host-armed fault injection (kFault* bits)
 };
+
+// Host-armed fault injection (never set in normal runs).
+constexpr uint32_t kFaultTileWait = 1u;  // the tile kernel's TMA barrier expects 16 bytes too many
 
 // ---- launch wrappers (mech_bin.cu) ----
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);

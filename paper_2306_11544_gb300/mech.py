@@ -43,7 +43,8 @@ EXPORTS = [
     "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
-    "mech_load_state", "mech_debug_bins", "mech_bin_noalloc", "mech_info", "mech_grid", "mech_destroy",
+    "mech_load_state", "mech_debug_bins", "mech_bin_noalloc", "mech_debug_inject", "mech_info", "mech_grid",
+    "mech_destroy",
 ]
 
 
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
             "mech_load_state": ([_P, _P, _P, _P, ctypes.c_int64], ctypes.c_int),
             "mech_debug_bins": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_bin_noalloc": ([ctypes.c_int64, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P], ctypes.c_int),
+            "mech_debug_inject": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_info": ([_P, _P], ctypes.c_int),
             "mech_grid": ([_P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
             "mech_destroy": ([_P], ctypes.c_int),
@@ -310,6 +312,15 @@ def mech_bin_noalloc(n, xyz_dev, lo, voxel, dims, key_dev, start_dev, order_dev,
                                            ctypes.c_void_p(int(key_dev)), ctypes.c_void_p(int(start_dev)),
                                            ctypes.c_void_p(int(order_dev)), _stream_handle(stream)),
            "mech_bin_noalloc")
+
+
+MECH_FAULT_NONE = 0
+MECH_FAULT_TILE_WAIT = 1
+MECH_FAULT_ALLOC = 2
+
+
+def mech_debug_inject(h, fault):
+    _check(load_library().mech_debug_inject(h, int(fault)), "mech_debug_inject")
 
 
 def mech_destroy(h):

@@ -76,3 +76,13 @@ def test_binding_raises_without_library(tmp_path):
             mech.load_library(str(tmp_path / "missing.so"))
     finally:
         mech._lib = saved
+
+
+def test_fault_injection_arming_is_host_only(lib):
+    """Arming and disarming the allocation fault needs no GPU; an unknown
+    fault or a missing handle for a handle-scoped fault is an argument error."""
+    from paper_2306_11544_gb300 import mech
+    assert lib.mech_debug_inject(None, mech.MECH_FAULT_ALLOC) == mech.MECH_OK
+    assert lib.mech_debug_inject(None, mech.MECH_FAULT_NONE) == mech.MECH_OK
+    assert lib.mech_debug_inject(None, mech.MECH_FAULT_TILE_WAIT) == mech.MECH_E_ARG
+    assert lib.mech_debug_inject(None, 99) == mech.MECH_E_ARG
