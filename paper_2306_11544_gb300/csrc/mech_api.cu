@@ -70,9 +70,6 @@ struct mech {
     std::vector<GridDev> grids;
     uint32_t V = 0, Vpad = 0;
     GridDev* d_grids = nullptr;
-    double* d_otab_d = nullptr;
-    float2* d_otab_f = nullptr;
-    size_t otab_cap = 0;
     size_t grid_cap = 0;
     // voxel tiles
     int ltx = 2, lty = 2, ltz = 2;
@@ -84,6 +81,8 @@ struct mech {
     uint8_t* d_tdense = nullptr;
     uint32_t* d_tlist = nullptr;
     uint32_t* d_ndense = nullptr;
+    uint32_t* d_slist = nullptr;
+    uint32_t* d_nsparse = nullptr;
     // state
     StateBuf st[2] = {};
     int cur = 0;
@@ -92,7 +91,6 @@ struct mech {
     double* d_cca64 = nullptr;
     // binning scratch
     uint32_t* d_key = nullptr;
-    uint32_t* d_slot = nullptr;
     uint32_t* d_vkey_s = nullptr;
     uint32_t* d_perm = nullptr;
     unsigned long long* d_tmp = nullptr;
@@ -180,12 +178,9 @@ struct mech {
         a.npad = npad;
         a.nrep = nrep;
         a.grids = d_grids;
-        a.otab_d = d_otab_d;
-        a.otab_f = d_otab_f;
         a.A = st[a_idx];
         a.B = st[a_idx ^ 1];
         a.key = d_key;
-        a.slot = d_slot;
         a.vkey_s = d_vkey_s;
         a.perm = d_perm;
         a.tmp = d_tmp;
@@ -215,7 +210,9 @@ struct mech {
         a.tdense = d_tdense;
         a.tlist = d_tlist;
         a.ndense = d_ndense;
-        a.Rmax_f = (float)maxR;
+        a.slist = d_slist;
+        a.nsparse = d_nsparse;
+        a.cut_eps = (float)(2e-5 * A * maxR);
         a.fault = fault;
         a.wait_ns = (fault & kFaultTileWait) ? 1000000ull : 2000000000ull;  // 1 ms armed, 2 s otherwise
         return a;
@@ -236,7 +233,6 @@ double voxel_of(const mech_t* h) { return h->voxel_int > 0.0 ? h->voxel_int : h-
 int build_grids(mech_t* h) {
     const double vx = voxel_of(h);
     std::vector<GridDev> g(h->nrep);
-    std::vector<double> otd;
     uint64_t vsum = 0, tsum = 0;
     for (int r = 0; r < h->nrep; ++r) {
         double lo[3], hi[3];
@@ -254,8 +250,6 @@ int build_grids(mech_t* h) {
             G.n[d] = (int32_t)nd;
             G.lo[d] = lo[d];
             G.lo_f[d] = (float)lo[d];
-            G.tab[d] = (uint32_t)otd.size();
-            for (int i = 0; i < G.n[d]; ++i) otd.push_back(lo[d] + (double)i * vx);
         }
         G.h = vx;
         G.inv_h = 1.0 / vx;
@@ -267,17 +261,21 @@ int build_grids(mech_t* h) {
         vsum += (uint64_t)G.n[0] * (uint64_t)G.n[1] * (uint64_t)G.n[2];
         const int lt[3] = {h->ltx, h->lty, h->ltz};
         for (int d = 0; d < 3; ++d) G.nt[d] = (G.n[d] + (1 << lt[d]) - 1) >> lt[d];
-        // hi grid: every value within (tile + 2 halo voxels) x 1.5 of reach stays below 2^23 q
-        const double reach = 1.5 * (double)((1 << std::max(h->ltx, std::max(h->lty, h->ltz))) + 2) * vx;
-        const int k = (int)std::floor(23.0 - std::log2(reach));
+        // record origin: the grid centre; hi grid q: 2^23 q covers twice the
+        // largest half-extent, so cells up to one half-extent outside the grid
+        // stay on it
+        double half = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            G.oc[d] = lo[d] + 0.5 * (double)G.n[d] * vx;
+            G.oc_hi[d] = (float)G.oc[d];
+            G.oc_lo[d] = (float)(G.oc[d] - (double)G.oc_hi[d]);
+            half = std::max(half, 0.5 * (double)G.n[d] * vx);
+        }
+        const int k = 23 - (int)std::ceil(std::log2(2.0 * half));
         G.q = (float)std::ldexp(1.0, -k);
         G.inv_q = (float)std::ldexp(1.0, k);
-        for (int d = 0; d < 3; ++d) {
-            const double w = (double)(1 << lt[d]) * vx;
-            const double wq = std::nearbyint(w / (double)G.q) * (double)G.q;
-            G.bwq[d] = (float)wq;
-            G.bwl[d] = (float)(w - wq);
-        }
+        G.qs = (float)std::ldexp(1.0, -k - 15);
+        G.qm = 2.0f * G.q;
         G.tbase = (uint32_t)tsum;
         tsum += (uint64_t)G.nt[0] * (uint64_t)G.nt[1] * (uint64_t)G.nt[2];
         if (vsum > (uint64_t)0x7FFFFFFF - 2 * (uint64_t)kScanTile)
@@ -325,23 +323,7 @@ int build_grids(mech_t* h) {
         MECH_TRY(h->alloc(&h->d_grids, (size_t)h->nrep));
         h->grid_cap = h->nrep;
     }
-    if (otd.size() > h->otab_cap) {
-        h->free_ptr(h->d_otab_d, h->otab_cap * sizeof(double));
-        h->free_ptr(h->d_otab_f, h->otab_cap * sizeof(float2));
-        h->d_otab_d = nullptr;
-        h->d_otab_f = nullptr;
-        MECH_TRY(h->alloc(&h->d_otab_d, otd.size()));
-        MECH_TRY(h->alloc(&h->d_otab_f, otd.size()));
-        h->otab_cap = otd.size();
-    }
-    std::vector<float2> otf(otd.size());
-    for (size_t i = 0; i < otd.size(); ++i) {
-        float hi = (float)otd[i];
-        otf[i] = make_float2(hi, (float)(otd[i] - (double)hi));
-    }
     CUDA_TRY(cudaMemcpyAsync(h->d_grids, g.data(), g.size() * sizeof(GridDev), cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d_otab_d, otd.data(), otd.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d_otab_f, otf.data(), otf.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[0], Vpad, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[1], Vpad, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_occ, Vpad / 32 + 1, h->stream));
@@ -368,8 +350,10 @@ int ready(mech_t* h) {
 int ensure_keys(mech_t* h) {
     if (h->keys_valid) return MECH_OK;
     StepArgs a = h->args(h->cur, 1);
-    CUDA_TRY(launch_zero_u32(h->d_count[h->cur], h->Vpad, h->stream));
-    CUDA_TRY(launch_zero_u32(h->d_tcount[h->cur], h->NT, h->stream));
+    for (int p = 0; p < 2; ++p) {  // this step's histograms are rebuilt; the next step's start from zero
+        CUDA_TRY(launch_zero_u32(h->d_count[p], h->Vpad, h->stream));
+        CUDA_TRY(launch_zero_u32(h->d_tcount[p], h->NT, h->stream));
+    }
     CUDA_TRY(launch_keys(a, h->elem_grid, h->stream));
     h->keys_valid = true;
     return MECH_OK;
@@ -381,7 +365,7 @@ int enqueue_step(mech_t* h, int integrate, bool profile = false) {
     cudaEvent_t* ev = nullptr;
     if (profile && h->prof_steps < mech::kProfCap) ev = &h->prof_ev[(size_t)h->prof_steps * (mech::kProfPhases + 1)];
     if (ev) CUDA_TRY(cudaEventRecord(ev[0], h->stream));
-    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, a.count_nxt, h->d_ndense, h->d_occ, h->stream));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, h->d_ndense, h->d_occ, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[1], h->stream));
     CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[2], h->stream));
@@ -391,6 +375,7 @@ int enqueue_step(mech_t* h, int integrate, bool profile = false) {
     if (ev) CUDA_TRY(cudaEventRecord(ev[4], h->stream));
     CUDA_TRY(launch_force_tiles(a, h->tile_grid, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[5], h->stream));
+    CUDA_TRY(launch_sparse_list(a, h->elem_grid, h->stream));
     CUDA_TRY(launch_force_cells(a, h->force_grid, h->force_block, h->stream));
     if (ev) {
         CUDA_TRY(cudaEventRecord(ev[6], h->stream));
@@ -507,7 +492,8 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (rc == MECH_OK) rc = h->alloc(&h->d_ccr64, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_cca64, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_key, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_slot, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_slist, np);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_nsparse, 1);
     if (rc == MECH_OK) rc = h->alloc(&h->d_vkey_s, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_perm, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_tmp, np);
@@ -523,8 +509,20 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     std::vector<float4> recp(n), recq(n);
     for (int64_t i = 0; i < n; ++i) {
         ids[i] = (uint32_t)i;
-        recp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), (float)R[i], 0.f);
+        // radius as FP32 + 16-bit residual in units of ulp(R) / 2^15 (upper half
+        // of recq.w); position residual fields start at zero (0x8000)
+        const float Rf = (float)R[i];
+        int e2 = 0;
+        std::frexp(Rf, &e2);  // Rf = m 2^e2, m in [0.5, 1): ulp = 2^(e2 - 24)
+        const double units = (R[i] - (double)Rf) / std::ldexp(1.0, e2 - 24);
+        const long L = std::lround(std::min(32767.0, std::max(-32768.0, units * 32768.0)));
+        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
+        float wzf, wxyf;
+        const uint32_t wxy = 0x80008000u;
+        std::memcpy(&wzf, &wzr, 4);
+        std::memcpy(&wxyf, &wxy, 4);
+        recp[i] = make_float4(0.f, 0.f, 0.f, Rf);
+        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), wxyf, wzf);
     }
     cudaStream_t s = h->stream;
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -891,15 +889,17 @@ int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, 
     h->keys_valid = false;
     MECH_TRY(ensure_keys(h));
     StepArgs a = h->args(h->cur, 1);
-    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, nullptr, h->d_occ, h->stream));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, h->d_occ, h->stream));
+    // the scatter counts the histogram back down to zero: copy it first
+    if (count) CUDA_TRY(cudaMemcpyAsync(count, a.count_cur, (size_t)h->V * 4, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
     CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
+    h->keys_valid = false;
     const size_t n = (size_t)h->n;
     std::vector<uint32_t> k(n), ids(n), perm(n);
     CUDA_TRY(cudaMemcpyAsync(k.data(), h->d_key, n * 4, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaMemcpyAsync(ids.data(), h->st[h->cur].id, n * 4, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaMemcpyAsync(perm.data(), h->d_perm, n * 4, cudaMemcpyDeviceToHost, h->stream));
-    if (count) CUDA_TRY(cudaMemcpyAsync(count, a.count_cur, (size_t)h->V * 4, cudaMemcpyDeviceToHost, h->stream));
     if (start) CUDA_TRY(cudaMemcpyAsync(start, h->d_start, ((size_t)h->V + 1) * 4, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (key)

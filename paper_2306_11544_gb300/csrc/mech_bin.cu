@@ -20,7 +20,7 @@ __global__ void k_zero_u32(uint32_t* __restrict__ p, size_t count) {
 }
 
 // Step 1a (first step after a state change): key of every cell in A order and
-// its arrival slot inside its voxel.  Loop is warp-uniform so that the
+// the histograms of voxels and tiles.  Loop is warp-uniform so that the
 // aggregated atomics always run on full warps.
 __global__ void k_keys(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -37,12 +37,9 @@ __global__ void k_keys(const StepArgs a) {
             key = cell_key(a.mode, g, a.A, a.npad, i, ix, iy, iz);
             tile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
-        const uint32_t slot = warp_count(a.count_cur, key, valid);
+        warp_add(a.count_cur, key, valid);
         warp_add(a.tcount_cur, tile, valid);
-        if (valid) {
-            a.key[i] = key;
-            a.slot[i] = slot;
-        }
+        if (valid) a.key[i] = key;
     }
 }
 
@@ -109,12 +106,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, 
     }
 }
 
-// start[v] = sum_{u<v} count[u]; each thread owns 16 consecutive voxels.  Also
-// clears the next step's histogram over the same range.
+// start[v] = sum_{u<v} count[u]; each thread owns 16 consecutive voxels, and
+// writes their occupancy bits.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ count,
                                                             const uint32_t* __restrict__ boff,
                                                             uint32_t* __restrict__ start,
-                                                            uint32_t* __restrict__ zero_next,
                                                             uint16_t* __restrict__ occ16) {
     __shared__ uint32_t sh[33];
     const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
@@ -149,21 +145,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
         }
         occ16[base / kScanItems] = (uint16_t)m;
     }
-    if (zero_next) {
-        uint4* z4 = reinterpret_cast<uint4*>(zero_next + base);
-#pragma unroll
-        for (int k = 0; k < kScanItems / 4; ++k) z4[k] = make_uint4(0u, 0u, 0u, 0u);
-    }
 }
 
 // Step 1c: every cell goes to start[key] + slot, carrying (id, A index).  The
-// slot order inside a voxel comes from atomics; k_canon makes it canonical.
+// slot is taken by counting the voxel's histogram entry back down, which
+// leaves the histogram zero for its reuse as the next step's accumulator; the
+// slot order inside a voxel comes from the atomics and k_canon makes it
+// canonical.
 __global__ void k_scatter(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const uint32_t k = a.key[i];
-        const uint32_t dst = a.start[k] + a.slot[i];
-        if (dst >= a.n) {  // only after an earlier device error left the keys inconsistent
+        const uint32_t left = atomicSub(&a.count_cur[k], 1u);  // cells of voxel k not yet placed
+        const uint32_t dst = a.start[k] + left - 1u;
+        if (left == 0u || dst >= a.n) {  // only after an earlier device error left the keys inconsistent
             atomicOr(a.err, kErrIndex);
             continue;
         }
@@ -172,13 +167,14 @@ __global__ void k_scatter(const StepArgs a) {
 }
 
 // Step 1d: rank each cell inside its voxel by caller index (ids are unique),
-// giving its final voxel-order position f; record perm[f], the key, and the
-// force record of the cell: its position relative to the origin of its tile
-// block split into a hi part on the power-of-two grid q and a residual lo
-// (recp = {hi.x, hi.y, hi.z, lo.z}), and the square roots of the coefficients,
-// the radius and lo.x, lo.y as a half2 in units of q (recq).
+// giving its final voxel-order position f; record perm[f], the key, the id,
+// the force record of the cell (position relative to the grid centre as hi on
+// the q grid + 16-bit residual, radius, coefficient square roots) and, in the
+// mixed modes, its state (position, compensation, previous velocity) in B
+// order for the force kernels.
 __global__ void k_canon(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const unsigned long long e = a.tmp[q];
         const uint32_t id = (uint32_t)(e >> 32);
@@ -201,40 +197,49 @@ __global__ void k_canon(const StepArgs a) {
         a.B.id[f] = id;  // written here, so the next state's slot map is complete even if a force kernel aborts
         const int r = rep_of_cell(a.grids, a.nrep, f);
         const GridDev& g = a.grids[r];
-        const uint32_t local = k - g.vbase;
-        const uint32_t ix = local % (uint32_t)g.n[0];
-        const uint32_t rest = local / (uint32_t)g.n[0];
-        const uint32_t iy = rest % (uint32_t)g.n[1];
-        const uint32_t iz = rest / (uint32_t)g.n[1];
-        // origin index of the tile block along each axis
-        const uint32_t ob[3] = {(ix >> a.ltx) << a.ltx, (iy >> a.lty) << a.lty, (iz >> a.ltz) << a.ltz};
-        // position relative to the block origin as hi (on the q grid) + lo
         float hi[3], lo[3];
         if (a.mode == kMixedKahan) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const float xh = a.A.posf[(size_t)d * a.npad + src];
-                const float c = a.A.comp[(size_t)d * a.npad + src];
-                const float2 o = a.otab_f[g.tab[d] + ob[d]];
-                // value = (x_hi - o.hi) - (o.lo + c), both sums error-free
+                const float xh = a.A.posf[d * np + src];
+                const float c = a.A.comp[d * np + src];
+                // value - centre = (x_hi - oc_hi) - (oc_lo + c), both sums error-free
                 float e1, e2;
-                const float s1 = two_sum(xh, -o.x, e1);
-                const float s = two_sum(s1, -__fadd_rn(o.y, c), e2);
-                hi[d] = quantize_hi(s, g.q, g.inv_q);
-                lo[d] = __fadd_rn(__fsub_rn(s, hi[d]), __fadd_rn(e1, e2));
+                const float s1 = two_sum(xh, -g.oc_hi[d], e1);
+                const float sv = two_sum(s1, -__fadd_rn(g.oc_lo[d], c), e2);
+                hi[d] = quantize_hi(sv, g.q, g.inv_q);
+                lo[d] = __fadd_rn(__fsub_rn(sv, hi[d]), __fadd_rn(e1, e2));
+                a.B.posf[d * np + f] = xh;
+                a.B.comp[d * np + f] = c;
+                a.B.vpf[d * np + f] = a.A.vpf[d * np + src];
             }
         } else {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double x = a.A.pos64[(size_t)d * a.npad + src];
-                const double r = __dsub_rn(x, a.otab_d[g.tab[d] + ob[d]]);
-                hi[d] = quantize_hi(__double2float_rn(r), g.q, g.inv_q);
-                lo[d] = __double2float_rn(__dsub_rn(r, (double)hi[d]));
+                const double x = a.A.pos64[d * np + src];
+                const double rr = __dsub_rn(x, g.oc[d]);
+                const double t = rint(__dmul_rn(rr, (double)g.inv_q));
+                if (fabs(t) < 8388608.0) {
+                    const double hd = __dmul_rn(t, (double)g.q);  // exact: integer times a power of two
+                    hi[d] = (float)hd;
+                    lo[d] = __double2float_rn(__dsub_rn(rr, hd));
+                } else {
+                    hi[d] = __double2float_rn(rr);
+                    lo[d] = 0.f;
+                }
+                if (a.mode == kMixedFP64Pos) {
+                    a.B.pos64[d * np + f] = x;
+                    a.B.vpf[d * np + f] = a.A.vpf[d * np + src];
+                }
             }
         }
-        const float4 qo = a.A.recq[src];
-        a.B.recp[f] = make_float4(hi[0], hi[1], hi[2], lo[2]);
-        a.B.recq[f] = make_float4(qo.x, qo.y, qo.z, pack_lo_xy(lo[0], lo[1], g.inv_q));
+        // radius, its residual and the coefficients travel with the record
+        const float4 pa = a.A.recp[src];
+        const float4 qa = a.A.recq[src];
+        const uint32_t wxy = fix16(lo[0] * g.inv_q) | (fix16(lo[1] * g.inv_q) << 16);
+        const uint32_t wzr = fix16(lo[2] * g.inv_q) | (__float_as_uint(qa.w) & 0xFFFF0000u);
+        a.B.recp[f] = make_float4(hi[0], hi[1], hi[2], pa.w);
+        a.B.recq[f] = make_float4(qa.x, qa.y, __uint_as_float(wxy), __uint_as_float(wzr));
     }
 }
 
@@ -331,12 +336,12 @@ cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start, uint32_t* zero_next,
-                        uint32_t* zero_word, uint32_t* occ, cudaStream_t s) {
+cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start, uint32_t* zero_word,
+                        uint32_t* occ, cudaStream_t s) {
     const uint32_t nb = vpad / kScanTile;
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(count, bsum);
     k_scan_top<<<1, 1024, 0, s>>>(bsum, nb, zero_word);
-    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, zero_next, reinterpret_cast<uint16_t*>(occ));
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, reinterpret_cast<uint16_t*>(occ));
     return cudaGetLastError();
 }
 

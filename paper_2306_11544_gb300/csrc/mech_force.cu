@@ -1,7 +1,7 @@
 // Neighbour-gather velocity and AB2 integration (steps 2 and 3 of the
 // mechanics update; the paper's "update velocity" region, Sec. 5.4).
 //
-// Mixed precision modes run three launches per step:
+// Mixed precision modes run four launches per step:
 //   k_tile_classify   flags every voxel tile (TX x TY x TZ voxels) holding at
 //                     least `dense_min` cells and lists the flagged tiles;
 //   k_force_tile      one CTA per dense tile: the rows of the tile's halo
@@ -9,25 +9,27 @@
 //                     voxel-sorted force records, so each row is staged into
 //                     shared memory by one TMA bulk copy; then one thread per
 //                     target cell tests its 27-voxel neighbourhood there;
-//   k_force_cells     one thread per remaining cell (sparse regions), reading
+//   k_sparse_list     lists the cells outside dense tiles;
+//   k_force_cells     one thread per listed cell (sparse regions), reading
 //                     its neighbours through L1.
 // The split is the GPU form of the paper's load-balance lesson (Sec. 5.4):
 // work follows voxel occupancy, dense regions are computed tile by tile in
 // mesh order (the coarse, cache-friendly grain the paper recommends) and empty
 // voxels cost nothing.
 //
-// Candidate tests use a conservative cutoff A (R_i + R_max) so that the loop
-// body is ~10 FP32 instructions; in the tile kernel the tests of 32 candidates
-// set bits of a hit mask and only the hits are then evaluated with the exact
-// cutoffs, so the expensive pair term never runs inside the scan.
+// Candidate tests compare the hi-part distance with A (R_i + R_j) plus a
+// margin of 2q (about 12 FP32 instructions per candidate); in the tile kernel
+// the tests of 32 candidates set bits of a hit mask and only the hits are then
+// evaluated exactly, so the pair term never runs inside the scan.
 // Every cell's sum is taken in the same candidate order: (dz, dy) rows in
 // lexicographic order, cells in voxel order inside a row.
 //
-// FP32 positions are relative to the origin of the cell's tile block, stored as
-// a hi part on a power-of-two grid plus a residual lo; the pair vector is
-// (hi_i - hi_j - o_hi) + (lo_i - lo_j - o_lo), o the block offset between the
-// two cells' blocks, exact up to its final rounding.  No FP64 arithmetic runs
-// in any candidate loop (FP64 is ~1/62 of FP32 throughput on this GPU).
+// Record positions are relative to the grid centre, split into a hi part on a
+// power-of-two grid q (differences of hi parts are exact) and a residual; the
+// pair vector (hi_i - hi_j) + (lo_i - lo_j) is exact up to its final rounding,
+// and records are used as staged, with no per-tile frame shift.  No FP64
+// arithmetic runs in any candidate loop (FP64 is ~1/62 of FP32 throughput on
+// this GPU).
 #include "mech_internal.cuh"
 
 namespace mk {
@@ -115,65 +117,114 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // ------------------------------------------------- shared arithmetic ----
 
-// Exact pair term (FP32) for a candidate at offset vector r = x_i - x_j with
-// squared length d2.  Adds (c_r - c_a) r / d to acc if 0 < d < A S.
-__device__ __forceinline__ void pair_term(float rx, float ry, float rz, float d2, float Ri, float Rj, float sccri,
-                                          float sccai, float sccrj, float sccaj, float A, float& ax, float& ay,
-                                          float& az) {
-    const float S = Ri + Rj;
+// Velocity sum with a Kahan compensation term per component: the sum of a
+// cell's pair terms is free of the cancellation error of a plain FP32 sum
+// (pair terms of a cell near force balance are much larger than their sum).
+struct Acc3 {
+    float x, y, z, cx, cy, cz;
+    __device__ __forceinline__ void zero() { x = y = z = cx = cy = cz = 0.f; }
+    __device__ __forceinline__ static void add1(float& s, float& c, float v) {
+        const float u = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, u);
+        c = __fsub_rn(__fsub_rn(t, s), u);
+        s = t;
+    }
+    __device__ __forceinline__ void add(float vx, float vy, float vz) {
+        add1(x, cx, vx);
+        add1(y, cy, vy);
+        add1(z, cz, vz);
+    }
+    __device__ __forceinline__ float vx() const { return __fsub_rn(x, cx); }
+    __device__ __forceinline__ float vy() const { return __fsub_rn(y, cy); }
+    __device__ __forceinline__ float vz() const { return __fsub_rn(z, cz); }
+};
+
+// Pair term (FP32) for a candidate at offset r = x_i - x_j, given as an exact
+// hi part h (a difference of values on the q grid) plus a small lo part l;
+// Rlo is the sum of the two radius residuals R - (float)R.  Adds
+// (c_r - c_a) r / d if 0 < d < A S.
+//   1 - d/S is formed as (S^2 - d^2) / (S (S + d)), with d^2 and S^2 carried
+//   as unevaluated sums (error-free products and sums), so the cancellation of
+//   1 - d/S near contact costs no accuracy: t and t_a are accurate to a few
+//   ulp even where d/S is close to 1, which a direct 1 - d/S is not.
+__device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
+                                          float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
+                                          float A, Acc3& acc) {
+    const float rx = hx + lx, ry = hy + ly, rz = hz + lz;
+    const float d2 = rx * rx + ry * ry + rz * rz;
+    float Se;
+    const float S = two_sum(Ri, Rj, Se);  // S + Se == Ri + Rj
+    Se += Rlo;
     const float AS = A * S;
     if (d2 < AS * AS && d2 > 0.f) {
+        // d^2 = D + De
+        const float px = hx * hx, py = hy * hy, pz = hz * hz;
+        float e1, e2;
+        const float D1 = two_sum(px, py, e1);
+        const float D = two_sum(D1, pz, e2);
+        const float De = ((fmaf(hx, hx, -px) + fmaf(hy, hy, -py)) + (fmaf(hz, hz, -pz) + (e1 + e2))) +
+                         (lx * (2.f * hx + lx) + ly * (2.f * hy + ly) + lz * (2.f * hz + lz));
         const float rd = rsqrtf(d2);
         const float d = d2 * rd;
-        const float ta = 1.f - __fdividef(d, AS);
+        // (A S)^2 - d^2, with A S = AS + eAS
+        const float eAS = fmaf(A, S, -AS) + A * Se;
+        const float A2 = AS * AS;
+        const float gA = (A2 - D) + ((fmaf(AS, AS, -A2) + 2.f * AS * eAS) - De);
+        const float ta = __fdividef(gA, AS * (AS + d));
         float cf = -(sccai * sccaj) * (ta * ta);
         if (d < S) {
-            const float t = 1.f - __fdividef(d, S);
+            const float S2 = S * S;
+            const float gS = (S2 - D) + ((fmaf(S, S, -S2) + 2.f * S * Se) - De);
+            const float t = __fdividef(gS, S * (S + d));
             cf += (sccri * sccrj) * (t * t);
         }
         const float sc = cf * rd;
-        ax += sc * rx;
-        ay += sc * ry;
-        az += sc * rz;
+        acc.add(sc * rx, sc * ry, sc * rz);
     }
 }
 
-// AB2 update of cell q (B order) from its A-order state; writes the B state and
-// returns the next step's voxel key, and its voxel coordinates.
+// Squared candidate cutoff for a target with cut_i = A R_i + margin.
+__device__ __forceinline__ bool candidate_hit(float hx, float hy, float hz, float A, float Rj, float cut_i) {
+    const float c = fmaf(A, Rj, cut_i);
+    return hx * hx + hy * hy + hz * hz < c * c;
+}
+
+// AB2 update of cell q (B order).  Its state was copied into B order by the
+// canonicalisation pass; it is read and updated in place.  Returns the next
+// step's voxel key and its voxel coordinates.
 template <int MODE>
 __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, float ax, float ay,
                                                  float az, int& nix, int& niy, int& niz) {
-    const uint32_t src = a.perm[q];
     const size_t np = a.npad;
     const float v[3] = {ax, ay, az};
     bool finite = true;
     float xf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const float vp = a.A.vpf[d * np + src];
+        const float vp = a.B.vpf[d * np + q];
         const float inc = a.dt_f * (1.5f * v[d] - 0.5f * vp);
         if (MODE == kMixedFP64Pos) {
-            const double x = a.A.pos64[d * np + src];
+            const double x = a.B.pos64[d * np + q];
             const double xn = a.integrate ? __dadd_rn(x, (double)inc) : x;
-            a.B.pos64[d * np + q] = xn;
+            if (a.integrate) a.B.pos64[d * np + q] = xn;
             xf[d] = __double2float_rn(xn);
             finite = finite && isfinite(xn);
         } else {
-            float xh = a.A.posf[d * np + src];
-            float cc = a.A.comp[d * np + src];
+            float xh = a.B.posf[d * np + q];
             if (a.integrate) {
+                float cc = a.B.comp[d * np + q];
                 const float y = __fsub_rn(inc, cc);
                 const float t = __fadd_rn(xh, y);
                 cc = __fsub_rn(__fsub_rn(t, xh), y);
                 xh = t;
+                a.B.posf[d * np + q] = xh;
+                a.B.comp[d * np + q] = cc;
             }
-            a.B.posf[d * np + q] = xh;
-            a.B.comp[d * np + q] = cc;
             xf[d] = xh;
             finite = finite && isfinite(xh);
         }
-        a.B.vpf[d * np + q] = a.integrate ? v[d] : vp;
-        if (!a.integrate) a.vout_f[d * np + q] = v[d];
+        if (a.integrate) a.B.vpf[d * np + q] = v[d];
+        else a.vout_f[d * np + q] = v[d];
         finite = finite && isfinite(v[d]);
     }
     if (!finite) atomicOr(a.err, kErrNonFinite);
@@ -183,16 +234,23 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
     return g.vbase + (uint32_t)nix + (uint32_t)g.n[0] * ((uint32_t)niy + (uint32_t)g.n[1] * (uint32_t)niz);
 }
 
+// Next-step histograms (voxels, tiles) and key of cell q; all 32 lanes call it.
+__device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, uint32_t nkey, uint32_t ntile,
+                                                 bool valid) {
+    warp_add(a.count_nxt, nkey, valid);
+    warp_add(a.tcount_nxt, ntile, valid);
+    if (valid) a.key[q] = nkey;
+}
+
 // Velocity of cell q by a direct walk over its 27 neighbour voxels in global
 // memory (L1-cached).  Candidate order: (dz, dy) rows, then voxel order.  The
 // occupancy bits of all nine rows are fetched first (independent loads), so
 // a cell with few or no neighbours costs one round of memory latency, not nine.
-// Candidates are tested on the hi parts with the conservative cutoff; a pair
-// that passes is evaluated from hi + lo.
+// Candidates are tested on the hi parts; a pair that passes is evaluated from
+// hi + lo.
 __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, const float4 pi,
-                                              const float4 qi, float& ax, float& ay, float& az) {
+                                              const float4 qi, Acc3& acc) {
     const float A = a.A_f;
-    const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
     const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
     const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
     const uint32_t wmask = (1u << (jx1 - jx0 + 1)) - 1u;
@@ -208,33 +266,26 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
             occ9 |= (w & wmask) << (3 * p);
         }
     }
-    const float2 lxy = unpack_lo_xy(qi.w, g.q);
-    const float cut = A * (qi.z + a.Rmax_f);
-    const float cut2 = cut * cut * 1.0001f;
-    ax = ay = az = 0.f;
+    const float4 li = record_lo(pi, qi, g.qs);
+    const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
+    acc.zero();
 #pragma unroll 1
     for (int p = 0; p < 9; ++p) {
         const uint32_t rb = (occ9 >> (3 * p)) & 7u;
         if (!rb) continue;
         const int jz = c.iz + p / 3 - 1, jy = c.iy + p % 3 - 1;
         const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
-        const float dbz = (float)((jz >> a.ltz) - biz), dby = (float)((jy >> a.lty) - biy);
-        const float oz = pi.z - dbz * g.bwq[2], ozl = pi.w - dbz * g.bwl[2];   // exact on the q grid
-        const float oy = pi.y - dby * g.bwq[1], oyl = lxy.y - dby * g.bwl[1];
         for (int jx = jx0; jx <= jx1; ++jx) {
             if (!((rb >> (jx - jx0)) & 1u)) continue;
             const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
-            const float dbx = (float)((jx >> a.ltx) - bix);
-            const float ox = pi.x - dbx * g.bwq[0], oxl = lxy.x - dbx * g.bwl[0];
             for (uint32_t j = s; j < e; ++j) {
                 const float4 pj = a.B.recp[j];
-                const float hx = ox - pj.x, hy = oy - pj.y, hz = oz - pj.z;
-                if (hx * hx + hy * hy + hz * hz < cut2) {
+                const float hx = pi.x - pj.x, hy = pi.y - pj.y, hz = pi.z - pj.z;
+                if (candidate_hit(hx, hy, hz, A, pj.w, cut_i)) {
                     const float4 qj = a.B.recq[j];
-                    const float2 lj = unpack_lo_xy(qj.w, g.q);
-                    const float rx = hx + (oxl - lj.x), ry = hy + (oyl - lj.y), rz = hz + (ozl - pj.w);
-                    pair_term(rx, ry, rz, rx * rx + ry * ry + rz * rz, qi.z, qj.z, qi.x, qi.y, qj.x, qj.y, A, ax, ay,
-                              az);
+                    const float4 lj = record_lo(pj, qj, g.qs);
+                    pair_term(hx, hy, hz, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w, li.w + lj.w, qi.x, qi.y,
+                              qj.x, qj.y, A, acc);
                 }
             }
         }
@@ -242,51 +293,47 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
 }
 
 // ------------------------------------------- thread-per-cell kernel ----
-// Every cell not owned by a dense tile (all cells when tiles are off).
+// Every cell not owned by a dense tile: the cells listed by k_sparse_list, or
+// all cells when tiles are off.
 template <int MODE>
 __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
-        const uint32_t q = base + lane;
-        bool work = q < a.n;
-        uint32_t nkey = 0, ntile = 0;
-        if (work) {
+    const uint32_t total = a.use_tiles ? *a.nsparse : a.n;
+    for (uint32_t base = warp * 32u; base < total; base += nwarps * 32u) {
+        const uint32_t idx = base + lane;
+        const bool valid = idx < total;
+        uint32_t q = 0, nkey = 0, ntile = 0;
+        if (valid) {
+            q = a.use_tiles ? a.slist[idx] : idx;
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(a.vkey_s[q], g);
-            if (a.use_tiles && a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)]) {
-                work = false;
-            } else {
-                float ax, ay, az;
-                velocity_walk(a, g, c, a.B.recp[q], a.B.recq[q], ax, ay, az);
-                int nix, niy, niz;
-                nkey = ab2_epilogue<MODE>(a, g, q, ax, ay, az, nix, niy, niz);
-                ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
-            }
+            Acc3 acc;
+            velocity_walk(a, g, c, a.B.recp[q], a.B.recq[q], acc);
+            int nix, niy, niz;
+            nkey = ab2_epilogue<MODE>(a, g, q, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
+            ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
         }
-        const uint32_t slot = warp_count(a.count_nxt, nkey, work);
-        warp_add(a.tcount_nxt, ntile, work);
-        if (work) {
-            a.key[q] = nkey;
-            a.slot[q] = slot;
-        }
+        next_step_counts(a, q, nkey, ntile, valid);
     }
 }
 
 // ----------------------------------------------------- tile classify ----
-// Flags dense tiles, lists them, clears the next step's tile histogram.
+// Flags dense tiles, lists them, clears the next step's tile histogram and the
+// sparse-cell counter.
 __global__ void k_tile_classify(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.nsparse = 0u;
     for (uint32_t base = warp * 32u; base < a.ntiles; base += nwarps * 32u) {
         const uint32_t t = base + lane;
         const bool valid = t < a.ntiles;
         bool dense = false;
         if (valid) {
-            dense = a.tcount_cur[t] >= a.dense_min;
+            dense = a.use_tiles && a.tcount_cur[t] >= a.dense_min;
             a.tdense[t] = dense ? 1 : 0;
             a.tcount_nxt[t] = 0u;
         }
@@ -298,6 +345,30 @@ __global__ void k_tile_classify(const StepArgs a) {
     }
 }
 
+// ------------------------------------------------------ sparse list ----
+// After the tile kernel (which may hand tiles back): B positions of every cell
+// whose tile is not dense, in runs of a warp's 32 consecutive cells.
+__global__ void k_sparse_list(const StepArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
+        const uint32_t q = base + lane;
+        bool sparse = false;
+        if (q < a.n) {
+            const int r = rep_of_cell(a.grids, a.nrep, q);
+            const GridDev& g = a.grids[r];
+            const Cell3 c = decode(a.vkey_s[q], g);
+            sparse = !a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)];
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, sparse);
+        uint32_t off = 0;
+        if (lane == 0 && m) off = atomicAdd(a.nsparse, (uint32_t)__popc(m));
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = q;
+    }
+}
+
 // --------------------------------------------------------- tile kernel ----
 // One CTA per dense tile of 4 x 4 x 4 voxels, per tile:
 //   1. halo row table: for each (y, z) row of the halo (one voxel around the
@@ -305,8 +376,6 @@ __global__ void k_tile_classify(const StepArgs a) {
 //      boundaries inside it;
 //   2. TMA: one bulk copy per row and array (positions, coefficients) into
 //      shared memory, completion on an mbarrier (bounded wait);
-//   3. the staged positions of halo cells that belong to neighbouring tile
-//      blocks are shifted into this tile's block frame, once per cell;
 //   4. for every core voxel, the shared-memory indices of its 27-voxel
 //      neighbourhood (9 contiguous row ranges) are written into one list;
 //   5. one thread per target cell scans its voxel's list 32 candidates at a
@@ -344,8 +413,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
     constexpr int LT = 2, T4 = 4, HX = T4 + 2, NROW = HX * HX, NVOX = T4 * T4 * T4;
     extern __shared__ __align__(128) unsigned char dsm[];
-    float4* sp = reinterpret_cast<float4*>(dsm);          // positions + radius (tile frame after step 3)
-    float4* sq = sp + kTCap;                              // coefficient square roots
+    float4* sp = reinterpret_cast<float4*>(dsm);          // hi positions + radius
+    float4* sq = sp + kTCap;                              // coefficient square roots + residuals
     uint16_t* clist = reinterpret_cast<uint16_t*>(sq + kTCap);   // per-voxel candidate lists
     __shared__ uint32_t s_row_gs[NROW];
     __shared__ uint32_t s_row_off[NROW + 1];
@@ -473,41 +542,6 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
             __syncthreads();
             continue;
         }
-        const float bwx = (float)T4 * g.h_f, bwy = bwx, bwz = bwx;
-        // 3b. shift halo cells of neighbouring blocks into this block's frame,
-        // one warp per halo row: hi by a multiple of the q-grid block width
-        // (exact), the remainder of the width into lo
-        {
-            const bool left = kx0 == 1;                       // row starts in block bx-1
-            const bool right = x_hi >= bx * T4 + T4;           // row ends in block bx+1
-            for (int rr = warp; rr < nrows; rr += kTT / 32) {
-                const int dby = ((y_lo + rr % nry) >> LT) - by;
-                const int dbz = ((z_lo + rr / nry) >> LT) - bz;
-                const uint32_t len = s_row_vb[rr][nrx];
-                const uint32_t lend = left ? s_row_vb[rr][1] : 0u;         // [0, lend): block bx-1
-                const uint32_t rbeg = right ? s_row_vb[rr][nrx - 1] : len;  // [rbeg, len): block bx+1
-                if (dby == 0 && dbz == 0 && lend == 0 && rbeg == len) continue;
-                float4* prow = sp + s_row_off[rr];
-                float4* qrow = sq + s_row_off[rr];
-                for (uint32_t li = lane; li < len; li += 32u) {
-                    const int dbx = li < lend ? -1 : (li >= rbeg ? 1 : 0);
-                    if (dbx | dby | dbz) {
-                        float4 p = prow[li];
-                        float4 qq = qrow[li];
-                        float2 l = unpack_lo_xy(qq.w, g.q);
-                        p.x += (float)dbx * g.bwq[0];
-                        p.y += (float)dby * g.bwq[1];
-                        p.z += (float)dbz * g.bwq[2];
-                        p.w += (float)dbz * g.bwl[2];
-                        l.x += (float)dbx * g.bwl[0];
-                        l.y += (float)dby * g.bwl[1];
-                        qq.w = pack_lo_xy(l.x, l.y, g.inv_q);
-                        prow[li] = p;
-                        qrow[li] = qq;
-                    }
-                }
-            }
-        }
         // 4b. candidate index lists, one (voxel, neighbour row) pair per thread
         for (int w = tid; w < nvox * 9; w += kTT) {
             const int v = w / 9, p = w - v * 9;
@@ -541,10 +575,10 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
                 const uint32_t si = s_row_off[rr] + s_row_vb[rr][kx] + k;
                 const float4 pi = sp[si];
                 const float4 qi = sq[si];
-                const float2 li = unpack_lo_xy(qi.w, g.q);
-                const float cut = A * (qi.z + a.Rmax_f);
-                const float cut2 = cut * cut * 1.0001f;
-                float ax = 0.f, ay = 0.f, az = 0.f;
+                const float4 li = record_lo(pi, qi, g.qs);
+                const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
+                Acc3 acc;
+                acc.zero();
                 // scan the list 32 candidates at a time: a branch-free test on the
                 // hi parts builds a hit mask, then the exact pair terms of the hits
                 // (from hi + lo) are summed in list order
@@ -555,9 +589,7 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
 #pragma unroll 8
                     for (uint32_t k = 0; k < nc; ++k) {
                         const float4 pj = sp[clist[cb + k]];
-                        const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
-                        const float d2 = rx * rx + ry * ry + rz * rz;
-                        hits |= (d2 < cut2 ? 1u : 0u) << k;
+                        hits |= (candidate_hit(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, A, pj.w, cut_i) ? 1u : 0u) << k;
                     }
                     while (hits) {
                         const uint32_t k = (uint32_t)(__ffs(hits) - 1);
@@ -565,24 +597,16 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
                         const uint32_t jj = clist[cb + k];
                         const float4 p2 = sp[jj];
                         const float4 q2 = sq[jj];
-                        const float2 l2 = unpack_lo_xy(q2.w, g.q);
-                        const float sx = (pi.x - p2.x) + (li.x - l2.x);
-                        const float sy = (pi.y - p2.y) + (li.y - l2.y);
-                        const float sz = (pi.z - p2.z) + (pi.w - p2.w);
-                        pair_term(sx, sy, sz, sx * sx + sy * sy + sz * sz, qi.z, q2.z, qi.x, qi.y, q2.x, q2.y, A, ax,
-                                  ay, az);
+                        const float4 l2 = record_lo(p2, q2, g.qs);
+                        pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y, li.z - l2.z, pi.w,
+                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, A, acc);
                     }
                 }
                 int nix, niy, niz;
-                nkey = ab2_epilogue<MODE>(a, g, q, ax, ay, az, nix, niy, niz);
+                nkey = ab2_epilogue<MODE>(a, g, q, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
                 ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
             }
-            const uint32_t slot = warp_count(a.count_nxt, nkey, valid);
-            warp_add(a.tcount_nxt, ntile, valid);
-            if (valid) {
-                a.key[q] = nkey;
-                a.slot[q] = slot;
-            }
+            next_step_counts(a, q, nkey, ntile, valid);
         }
         __syncthreads();  // shared tables and records are reused by the next tile
     }
@@ -614,31 +638,27 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
             const uint32_t idi = a.A.id[src];
             const double xi = a.A.pos64[src], yi = a.A.pos64[np + src], zi = a.A.pos64[2 * np + src];
             const double Ri = a.R64[idi], ccri = a.ccr64[idi], ccai = a.cca64[idi];
-            const float bwx = g.bwq[0], bwy = g.bwq[1], bwz = g.bwq[2];
-            const float ASf = A * (a.B.recq[q].z + a.Rmax_f);  // conservative: the largest partner radius
-            const int bix = c.ix >> a.ltx, biy = c.iy >> a.lty, biz = c.iz >> a.ltz;
+            const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int dz = -1; dz <= 1; ++dz) {
                 const int jz = c.iz + dz;
                 if (jz < 0 || jz >= g.n[2]) continue;
-                const float oz = pi.z - (float)((jz >> a.ltz) - biz) * bwz;
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int jy = c.iy + dy;
                     if (jy < 0 || jy >= g.n[1]) continue;
-                    const float oy = pi.y - (float)((jy >> a.lty) - biy) * bwy;
                     const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
                     const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
                     const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
                     uint32_t s = a.start[row + jx0];
                     for (int jx = jx0; jx <= jx1; ++jx) {
                         const uint32_t e = a.start[row + jx + 1];
-                        const float ox = pi.x - (float)((jx >> a.ltx) - bix) * bwx;
                         for (uint32_t j = s; j < e; ++j) {
                             if (j == q) continue;
                             const float4 pj = a.B.recp[j];
-                            const float rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
+                            const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
                             const float d2f = rx * rx + ry * ry + rz * rz;
-                            if (!(d2f <= ASf * ASf * 1.0001f + 1e-2f)) continue;
+                            const float cut = fmaf(A, pj.w, cut_i);
+                            if (!(d2f <= cut * cut * 1.0001f + 1e-2f)) continue;
                             const uint32_t sj = a.perm[j];
                             const uint32_t idj = a.A.id[sj];
                             const double dx = __dsub_rn(xi, a.A.pos64[sj]);
@@ -692,12 +712,7 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
             nkey = g.vbase + (uint32_t)ix + (uint32_t)g.n[0] * ((uint32_t)iy + (uint32_t)g.n[1] * (uint32_t)iz);
             ntile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
-        const uint32_t slot = warp_count(a.count_nxt, nkey, valid);
-        warp_add(a.tcount_nxt, ntile, valid);
-        if (valid) {
-            a.key[q] = nkey;
-            a.slot[q] = slot;
-        }
+        next_step_counts(a, q, nkey, ntile, valid);
     }
 }
 
@@ -751,6 +766,12 @@ cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
     if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos>(a, grid, s);
     return launch_tile_mode<kMixedKahan>(a, grid, s);
+}
+
+cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
+    k_sparse_list<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStream_t s) {

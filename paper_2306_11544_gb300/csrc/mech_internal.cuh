@@ -10,32 +10,36 @@
 //       vp64   [3][npad] double   previous velocity (FP64 mode)
 //       vpf    [3][npad] float    previous velocity (mixed modes)
 //       id     [n]       u32      caller index of the cell
-//       recp   [n]       float4   {x_hi, y_hi, z_hi, z_lo}: position relative to
-//                                 the origin of the cell's tile block (below) as
-//                                 a hi part on a fixed power-of-two grid q plus
-//                                 a small residual lo
-//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), R, half2(x_lo/q, y_lo/q)}
-//   * binning scratch: key/slot [n] (key and within-voxel arrival slot of
-//     each cell in A order), vkey_s [n] (key in B order), perm [n] (A index of
-//     the cell at each B position), tmp [n] u64 (id << 32 | A index, scattered
-//     by key), count[2][Vpad] (histograms of this and the next step),
-//     start[Vpad] (exclusive scan of count: cells of voxel v are the sorted
-//     positions start[v] .. start[v+1]-1), occ[Vpad/32 + 1] (bit v: count > 0).
+//       recp   [n]       float4   {x_hi, y_hi, z_hi, R}: position relative to
+//                                 the replicate's grid centre as a hi part on
+//                                 a power-of-two grid q, and the radius (FP32)
+//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), lo_xy, lo_zr}: the
+//                                 coefficient square roots, then four 16-bit
+//                                 fixed-point residuals: x_lo, y_lo, z_lo in
+//                                 units of q / 2^15 and R - (float)R in units
+//                                 of ulp(R) / 2^15
+//     The canonicalisation pass also copies each cell's state (positions,
+//     compensation, previous velocity) into B order, so the force kernels
+//     read and update their own cells contiguously.
+//   * binning scratch: key [n] (next voxel of each cell in A order), vkey_s
+//     [n] (key in B order), perm [n] (A index of the cell at each B
+//     position), tmp [n] u64 (id << 32 | A index, scattered by key),
+//     count[2][Vpad] (histograms of this and the next step; the scatter
+//     counts this step's histogram back down to zero), start[Vpad] (exclusive
+//     scan of count: cells of voxel v are the sorted positions start[v] ..
+//     start[v+1]-1), occ[Vpad/32 + 1] (bit v: count > 0).
 //   * voxel tiles: the grid is cut into blocks of TX x TY x TZ voxels (powers
 //     of two); tcount[2][T] counts the cells of each tile (this step, next
 //     step), tdense[T] flags the tiles processed by the shared-memory tile
-//     kernel and tlist holds their indices (ndense of them).
-//   * per-replicate grid descriptors and per-axis voxel-origin tables.
+//     kernel and tlist holds their indices (ndense of them); slist holds the
+//     B positions of the other cells (nsparse of them).
+//   * per-replicate grid descriptors.
 //
-// FP32 positions in the force record are relative to the origin of the cell's
-// tile block (voxel index rounded down to a multiple of the tile size), so one
-// row of a tile halo copied verbatim into shared memory needs an offset only
-// where it crosses into a neighbouring block.  The hi parts and the block
-// widths lie on a grid of spacing q = 2^-k chosen so that every hi value, block
-// offset and their sums and differences within a tile's reach are exactly
-// representable in FP32; a pair's relative vector is then
-// (hi_i - hi_j - offset_hi) + (lo_i - lo_j - offset_lo), exact up to its final
-// rounding.  Candidate tests use the hi parts only (error <= q).
+// Record positions: every hi part is an integer multiple of q with magnitude
+// below 2^23 q, so hi_i - hi_j is exact in FP32 for any two cells of a
+// replicate, and a pair's relative vector (hi_i - hi_j) + (lo_i - lo_j) is
+// exact up to its final rounding.  Candidate tests use the hi parts with a
+// margin of 2q.
 #pragma once
 
 #include <cstdint>
@@ -68,32 +72,47 @@ struct GridDev {
     uint32_t vbase;    // first global voxel index of this replicate
     uint32_t cbase;    // first cell (same in caller and voxel order)
     uint32_t ncell;
-    uint32_t tab[3];   // offset of each axis in the origin tables
     int32_t nt[3];     // tiles per axis
     uint32_t tbase;    // first global tile index of this replicate
-    float q, inv_q;    // grid of the hi parts of record positions (a power of two)
-    float bwq[3];      // tile-block width per axis rounded to the q grid
-    float bwl[3];      // the remainder of the block width (FP64 width - bwq)
+    double oc[3];      // grid centre: origin of the record positions
+    float oc_hi[3], oc_lo[3];  // the centre as an exact FP32 pair
+    float q, inv_q;    // grid of the hi parts (a power of two)
+    float qs;          // q / 2^15: unit of the 16-bit position residuals
+    float qm;          // candidate-test margin (>= 2 q)
 };
 
-// Split of a position p (relative to its tile-block origin) into a hi part on
-// the q grid and a residual; lo is stored scaled by 1/q as FP16 for x and y.
-__device__ __forceinline__ float quantize_hi(float p, float q, float inv_q) {
-    const float t = p * inv_q;
-    return fabsf(t) < 8388608.f ? rintf(t) * q : p;
+// Position relative to the grid centre -> hi on the q grid (|hi| < 2^23 q);
+// the residual r - hi is at most q/2.  A cell beyond 2^23 q (far outside its
+// grid) keeps hi = r and lo = 0: its pair vectors are rounded once.
+__device__ __forceinline__ float quantize_hi(float r, float q, float inv_q) {
+    const float t = r * inv_q;
+    return fabsf(t) < 8388608.f ? rintf(t) * q : r;
 }
 
-__device__ __forceinline__ float pack_lo_xy(float lx, float ly, float inv_q) {
-    const float sx = fminf(fmaxf(lx * inv_q, -60000.f), 60000.f);
-    const float sy = fminf(fmaxf(ly * inv_q, -60000.f), 60000.f);
-    const __half2 h = __floats2half2_rn(sx, sy);
-    return *reinterpret_cast<const float*>(&h);
+// 16-bit fixed point with offset 2^15: v in [-1, 1) units -> [0, 65535].
+__device__ __forceinline__ uint32_t fix16(float v_units) {
+    const float t = fminf(fmaxf(rintf(v_units * 32768.f), -32768.f), 32767.f);
+    return (uint32_t)((int)t + 32768);
 }
 
-__device__ __forceinline__ float2 unpack_lo_xy(float w, float q) {
-    const __half2 h = *reinterpret_cast<const __half2*>(&w);
-    const float2 f = __half22float2(h);
-    return make_float2(f.x * q, f.y * q);
+// 16-bit field u (offset 2^15) scaled by s (a power of two), exactly:
+// 0x4B000000 | u is the float 2^23 + u, and (2^23 + u) s - (2^23 + 2^15) s is
+// (u - 2^15) s without rounding.
+__device__ __forceinline__ float unfix16(uint32_t u16, float s) {
+    return fmaf(__int_as_float(0x4B000000u | u16), s, -8421376.f * s);
+}
+
+// Scale of the radius residual: ulp(R) / 2^15 for a normal R > 2^-87.
+__device__ __forceinline__ float rlo_scale(float R) {
+    return __int_as_float((int)(__float_as_uint(R) & 0x7F800000u) - ((23 + 15) << 23));
+}
+
+// Position residuals and radius residual of a record: {x_lo, y_lo, z_lo, R_lo}
+// (qs = q / 2^15).
+__device__ __forceinline__ float4 record_lo(const float4 p, const float4 c, float qs) {
+    const uint32_t wxy = __float_as_uint(c.z), wzr = __float_as_uint(c.w);
+    return make_float4(unfix16(wxy & 0xFFFFu, qs), unfix16(wxy >> 16, qs), unfix16(wzr & 0xFFFFu, qs),
+                       unfix16(wzr >> 16, rlo_scale(p.w)));
 }
 
 // Error-free sum: s + e == a + b exactly (Knuth).
@@ -121,11 +140,8 @@ struct StepArgs {
     uint32_t npad;
     int nrep;
     const GridDev* grids;
-    const double* otab_d;  // voxel origin lo_d + i h per axis index, FP64
-    const float2* otab_f;  // the same origin as an exact FP32 pair (hi, lo)
     StateBuf A, B;
     uint32_t* key;
-    uint32_t* slot;
     uint32_t* vkey_s;
     uint32_t* perm;
     unsigned long long* tmp;
@@ -152,7 +168,9 @@ struct StepArgs {
     uint8_t* tdense;
     uint32_t* tlist;
     uint32_t* ndense;
-    float Rmax_f;          // largest radius (conservative candidate cutoff)
+    uint32_t* slist;       // B positions of the cells outside dense tiles
+    uint32_t* nsparse;
+    float cut_eps;         // candidate-test margin for FP32 rounding (added to each grid's qm)
     unsigned long long wait_ns;  // time limit of every device-side wait
     uint32_t fault;        // host-armed fault injection (kFault* bits)
 };
@@ -164,7 +182,7 @@ constexpr uint32_t kFaultTileWait = 1u;  // the tile kernel's TMA barrier expect
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
 cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start,
-                        uint32_t* zero_next, uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
+                        uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
 cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);
@@ -184,6 +202,7 @@ int record_error(int code, const std::string& msg);
 // that it can be timed; `ev` (may be null) receives an event between phases.
 cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStream_t s);
 int force_max_blocks_per_sm(int mode, int block);
 int tile_kernel_grid(const StepArgs& a, int sms);

@@ -156,7 +156,7 @@ extern "C" int mech_bin_noalloc(int64_t n, const double* xyz, const double lo[3]
                                         key, slot);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = launch_scan(count, vpad, bsum, sstart, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = launch_scan(count, vpad, bsum, sstart, nullptr, nullptr, s);
     if (e == cudaSuccess && nn) {
         k_na_scatter<<<grid, 256, 0, s>>>(nn, key, slot, sstart, tmp);
         e = cudaGetLastError();
