@@ -237,9 +237,11 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
 // Next-step histograms (voxels, tiles) and key of cell q; all 32 lanes call it.
 __device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, uint32_t nkey, uint32_t ntile,
                                                  bool valid) {
-    warp_add(a.count_nxt, nkey, valid);
-    warp_add(a.tcount_nxt, ntile, valid);
-    if (valid) a.key[q] = nkey;
+    warp_add(a.tcount_nxt, ntile, valid);  // many lanes share a tile: aggregate
+    if (valid) {
+        atomicAdd(&a.count_nxt[nkey], 1u);  // voxels hold ~2 cells: plain reduction
+        a.key[q] = nkey;
+    }
 }
 
 // Velocity of cell q by a direct walk over its 27 neighbour voxels in global
@@ -320,6 +322,16 @@ __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
     }
 }
 
+// A tile is processed by the tile kernel only when its whole halo lies inside
+// the grid (1 <= b and 4 b + 4 <= n - 1 on every axis): the kernel's shape is
+// then fixed (6 x 6 halo rows of 6 voxels around 4 x 4 x 4 core voxels) and its
+// index arithmetic compiles to constants.  Tiles at the grid faces go to the
+// thread-per-cell kernel.
+__device__ __forceinline__ bool tile_interior(const GridDev& g, int bx, int by, int bz) {
+    return bx >= 1 && by >= 1 && bz >= 1 && 4 * bx + 4 <= g.n[0] - 1 && 4 * by + 4 <= g.n[1] - 1 &&
+           4 * bz + 4 <= g.n[2] - 1;
+}
+
 // ----------------------------------------------------- tile classify ----
 // Flags dense tiles, lists them, clears the next step's tile histogram and the
 // sparse-cell counter.
@@ -334,6 +346,14 @@ __global__ void k_tile_classify(const StepArgs a) {
         bool dense = false;
         if (valid) {
             dense = a.use_tiles && a.tcount_cur[t] >= a.dense_min;
+            if (dense) {
+                const int r = rep_of_tile(a.grids, a.nrep, t);
+                const GridDev& g = a.grids[r];
+                const uint32_t lt = t - g.tbase;
+                const uint32_t rest = lt / (uint32_t)g.nt[0];
+                dense = tile_interior(g, (int)(lt % (uint32_t)g.nt[0]), (int)(rest % (uint32_t)g.nt[1]),
+                                      (int)(rest / (uint32_t)g.nt[1]));
+            }
             a.tdense[t] = dense ? 1 : 0;
             a.tcount_nxt[t] = 0u;
         }
@@ -405,24 +425,25 @@ __device__ __forceinline__ uint32_t warp_scan_inplace(uint32_t* v, int n) {
 }
 
 constexpr int kTT = 160;          // threads per tile CTA (about one target each)
-constexpr int kTCap = 768;        // staged halo records per tile
+constexpr int kTCap = 640;        // staged halo records per tile (a dense core tile holds ~490)
 constexpr int kTListCap = 5120;   // candidate-list entries per tile
 constexpr size_t kTileDynSmem = (size_t)kTCap * 2 * sizeof(float4) + (size_t)kTListCap * 2;
 
 template <int MODE>
-__global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
-    constexpr int LT = 2, T4 = 4, HX = T4 + 2, NROW = HX * HX, NVOX = T4 * T4 * T4;
+__global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
+    constexpr int HX = 6, NB = HX + 1, NROW = HX * HX, NVOX = 64;
     extern __shared__ __align__(128) unsigned char dsm[];
     float4* sp = reinterpret_cast<float4*>(dsm);          // hi positions + radius
     float4* sq = sp + kTCap;                              // coefficient square roots + residuals
     uint16_t* clist = reinterpret_cast<uint16_t*>(sq + kTCap);   // per-voxel candidate lists
     __shared__ uint32_t s_row_gs[NROW];
     __shared__ uint32_t s_row_off[NROW + 1];
-    __shared__ uint32_t s_row_vb[NROW][HX + 1];
+    __shared__ uint32_t s_row_vb[NROW][NB];
     __shared__ uint32_t s_vox_loff[NVOX + 1];   // list offset of each core voxel
     __shared__ uint32_t s_vox_toff[NVOX + 1];   // first target number of each core voxel
     __shared__ uint16_t s_vp_off[NVOX][9];      // offset of each neighbour row inside a voxel's list
-    __shared__ int s_flag;                       // TMA timeout
+    __shared__ uint8_t s_tvox[kTCap];           // core voxel of each target
+    __shared__ int s_flag;                       // copy timeout
     __shared__ __align__(8) uint64_t s_bar;
 
     const int tid = threadIdx.x;
@@ -446,86 +467,75 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
         const uint32_t rest = lt / (uint32_t)g.nt[0];
         const int by = (int)(rest % (uint32_t)g.nt[1]);
         const int bz = (int)(rest / (uint32_t)g.nt[1]);
-        const int x_lo = max(bx * T4 - 1, 0), x_hi = min(bx * T4 + T4, g.n[0] - 1);
-        const int y_lo = max(by * T4 - 1, 0), y_hi = min(by * T4 + T4, g.n[1] - 1);
-        const int z_lo = max(bz * T4 - 1, 0), z_hi = min(bz * T4 + T4, g.n[2] - 1);
-        const int nrx = x_hi - x_lo + 1, nry = y_hi - y_lo + 1, nrz = z_hi - z_lo + 1;
-        const int nrows = nry * nrz;
-        const int kx0 = bx * T4 - x_lo;
-        const int ncx = min(T4, g.n[0] - bx * T4), ncy = min(T4, g.n[1] - by * T4), ncz = min(T4, g.n[2] - bz * T4);
-        const int nvox = ncx * ncy * ncz;
-        // 1. halo row table, one (row, boundary) pair per thread
-        for (int w = tid; w < nrows * (nrx + 1); w += kTT) {
-            const int rr = w / (nrx + 1), k = w - rr * (nrx + 1);
-            const int yy = y_lo + rr % nry, zz = z_lo + rr / nry;
+        const int x_lo = 4 * bx - 1, y_lo = 4 * by - 1, z_lo = 4 * bz - 1;
+        // 1. halo row table: row rr = (y - y_lo) + 6 (z - z_lo); boundary k of a
+        // row is the start of its voxel x_lo + k (k = 6: the end of the row)
+        for (int w = tid; w < NROW * NB; w += kTT) {
+            const int rr = w / NB, k = w - rr * NB;
+            const int yy = y_lo + rr % HX, zz = z_lo + rr / HX;
             const uint32_t rowv = g.vbase + (uint32_t)g.n[0] * ((uint32_t)yy + (uint32_t)g.n[1] * (uint32_t)zz);
-            s_row_vb[rr][k] = a.start[rowv + x_lo + k];
+            s_row_vb[rr][k] = a.start[rowv + (uint32_t)(x_lo + k)];
         }
         __syncthreads();
         if (warp == 0) {
-            for (int rr = (int)lane; rr < nrows; rr += 32) {
+            for (int rr = (int)lane; rr < NROW; rr += 32) {
                 const uint32_t gs = s_row_vb[rr][0];
                 s_row_gs[rr] = gs;
-                s_row_off[rr] = s_row_vb[rr][nrx] - gs;  // row length, scanned below
+                s_row_off[rr] = s_row_vb[rr][HX] - gs;  // row length, scanned below
             }
             __syncwarp();
-            const uint32_t total = warp_scan_inplace(s_row_off, nrows);
-            if (lane == 0) s_row_off[nrows] = total;
+            const uint32_t total = warp_scan_inplace(s_row_off, NROW);
+            if (lane == 0) s_row_off[NROW] = total;
         }
         __syncthreads();
-        for (int w = tid; w < nrows * (nrx + 1); w += kTT) {
-            const int rr = w / (nrx + 1), k = w - rr * (nrx + 1);
+        for (int w = tid; w < NROW * NB; w += kTT) {
+            const int rr = w / NB, k = w - rr * NB;
             s_row_vb[rr][k] -= s_row_gs[rr];  // boundaries relative to the row start
         }
-        const uint32_t total = s_row_off[nrows];
+        const uint32_t total = s_row_off[NROW];
         __syncthreads();
         if (total > (uint32_t)kTCap) {  // does not fit: leave the tile to the thread-per-cell kernel
             if (tid == 0) a.tdense[tile] = 0;
             continue;
         }
-        // 2. TMA bulk copies of the halo rows
-        if (warp == 0) {
-            if (lane == 0) {
-                fence_proxy_async();
+        // 2. TMA bulk copies of the halo rows, one row per thread; the barrier
+        // expects the bytes of all rows (its single arrival comes with them)
+        if (tid < NROW) {
+            const int rr = tid;
+            const uint32_t len = s_row_vb[rr][HX];
+            fence_proxy_async();
+            if (tid == 0)
                 mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4) +
                                                   ((a.fault & kFaultTileWait) ? 16u : 0u));
+            if (len) {
+                bulk_g2s(&sp[s_row_off[rr]], &a.B.recp[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
+                bulk_g2s(&sq[s_row_off[rr]], &a.B.recq[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
             }
-            __syncwarp();
-            for (int rr = (int)lane; rr < nrows; rr += 32) {
-                const uint32_t len = s_row_vb[rr][nrx];
-                if (len) {
-                    bulk_g2s(&sp[s_row_off[rr]], &a.B.recp[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
-                    bulk_g2s(&sq[s_row_off[rr]], &a.B.recq[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
-                }
-            }
-        }
-        // 4a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
-        if (tid < nvox) {
-            const int v = tid;
-            const int kx = kx0 + v % ncx;
-            const int yy = by * T4 + (v / ncx) % ncy, zz = bz * T4 + v / (ncx * ncy);
-            const int ka = max(kx - 1, 0), kb = min(kx + 1, nrx - 1);
+        } else if (tid >= 64 && tid < 64 + NVOX) {
+            // 4a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
+            const int v = tid - 64;
+            const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
             uint32_t len = 0;
             int p = 0;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy, ++p) {
-                    const int z2 = zz + dz, y2 = yy + dy;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy, ++p) {
+                    const int r2 = (cy + dy) + HX * (cz + dz);
                     s_vp_off[v][p] = (uint16_t)len;
-                    if (z2 < z_lo || z2 > z_hi || y2 < y_lo || y2 > y_hi) continue;
-                    const int r2 = (y2 - y_lo) + nry * (z2 - z_lo);
-                    len += s_row_vb[r2][kb + 1] - s_row_vb[r2][ka];
+                    len += s_row_vb[r2][cx + 3] - s_row_vb[r2][cx];
                 }
-            const int rr = (yy - y_lo) + nry * (zz - z_lo);
+            const int rr = (cy + 1) + HX * (cz + 1);
             s_vox_loff[v] = len;
-            s_vox_toff[v] = s_row_vb[rr][kx + 1] - s_row_vb[rr][kx];
+            s_vox_toff[v] = s_row_vb[rr][cx + 2] - s_row_vb[rr][cx + 1];
         }
         __syncthreads();
         if (warp == 0) {
-            const uint32_t l_total = warp_scan_inplace(s_vox_loff, nvox);
-            const uint32_t t_total = warp_scan_inplace(s_vox_toff, nvox);
+            const uint32_t l_total = warp_scan_inplace(s_vox_loff, NVOX);
+            const uint32_t t_total = warp_scan_inplace(s_vox_toff, NVOX);
             if (lane == 0) {
-                s_vox_loff[nvox] = l_total;
-                s_vox_toff[nvox] = t_total;
+                s_vox_loff[NVOX] = l_total;
+                s_vox_toff[NVOX] = t_total;
             }
         }
         // 3. wait for the halo
@@ -537,64 +547,71 @@ __global__ void __launch_bounds__(kTT, 5) k_force_tile(const StepArgs a) {
             mbar_wait_bounded(&s_bar, phase ^ 1u, a.wait_ns);  // let copies in flight land first
             return;
         }
-        if (s_vox_loff[nvox] > (uint32_t)kTListCap) {  // lists do not fit: same hand-back
+        if (s_vox_loff[NVOX] > (uint32_t)kTListCap) {  // lists do not fit: same hand-back
             if (tid == 0) a.tdense[tile] = 0;
             __syncthreads();
             continue;
         }
-        // 4b. candidate index lists, one (voxel, neighbour row) pair per thread
-        for (int w = tid; w < nvox * 9; w += kTT) {
+        // 4b. candidate index lists, one (voxel, neighbour row) pair per thread,
+        // and the core voxel of every target
+        for (int w = tid; w < NVOX * 9; w += kTT) {
             const int v = w / 9, p = w - v * 9;
-            const int dz = p / 3 - 1, dy = p % 3 - 1;
-            const int kx = kx0 + v % ncx;
-            const int y2 = by * T4 + (v / ncx) % ncy + dy, z2 = bz * T4 + v / (ncx * ncy) + dz;
-            if (z2 < z_lo || z2 > z_hi || y2 < y_lo || y2 > y_hi) continue;
-            const int ka = max(kx - 1, 0), kb = min(kx + 1, nrx - 1);
-            const int r2 = (y2 - y_lo) + nry * (z2 - z_lo);
+            const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
+            const int r2 = (cy + p % 3) + HX * (cz + p / 3);
             uint32_t o = s_vox_loff[v] + s_vp_off[v][p];
-            const uint32_t j1 = s_row_off[r2] + s_row_vb[r2][kb + 1];
-            for (uint32_t j = s_row_off[r2] + s_row_vb[r2][ka]; j < j1; ++j) clist[o++] = (uint16_t)j;
+            const uint32_t j1 = s_row_off[r2] + s_row_vb[r2][cx + 3];
+            for (uint32_t j = s_row_off[r2] + s_row_vb[r2][cx]; j < j1; ++j) clist[o++] = (uint16_t)j;
+            if (p == 0)
+                for (uint32_t t = s_vox_toff[v]; t < s_vox_toff[v + 1]; ++t) s_tvox[t] = (uint8_t)v;
         }
         __syncthreads();
         // 5. one thread per target
-        const uint32_t T = s_vox_toff[nvox];
+        const uint32_t T = s_vox_toff[NVOX];
         for (uint32_t t0 = (uint32_t)warp * 32u; t0 < T; t0 += kTT) {
             const uint32_t t = t0 + lane;
             const bool valid = t < T;
             uint32_t nkey = 0, ntile = 0, q = 0;
             if (valid) {
-                int v = 0, vhi = nvox - 1;  // core voxel of target t
-                while (v < vhi) {
-                    const int mid = (v + vhi + 1) >> 1;
-                    if (s_vox_toff[mid] <= t) v = mid; else vhi = mid - 1;
-                }
+                const int v = s_tvox[t];
                 const uint32_t k = t - s_vox_toff[v];
-                const int kx = kx0 + v % ncx;
-                const int rr = (by * T4 + (v / ncx) % ncy - y_lo) + nry * (bz * T4 + v / (ncx * ncy) - z_lo);
-                q = s_row_gs[rr] + s_row_vb[rr][kx] + k;
-                const uint32_t si = s_row_off[rr] + s_row_vb[rr][kx] + k;
+                const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
+                const int rr = (cy + 1) + HX * (cz + 1);
+                const uint32_t in_row = s_row_vb[rr][cx + 1] + k;
+                q = s_row_gs[rr] + in_row;
+                const uint32_t si = s_row_off[rr] + in_row;
                 const float4 pi = sp[si];
                 const float4 qi = sq[si];
                 const float4 li = record_lo(pi, qi, g.qs);
                 const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
                 Acc3 acc;
                 acc.zero();
-                // scan the list 32 candidates at a time: a branch-free test on the
-                // hi parts builds a hit mask, then the exact pair terms of the hits
-                // (from hi + lo) are summed in list order
+                // scan the list in blocks of 32 candidates (up to three blocks at a
+                // time): a branch-free test on the hi parts builds one hit mask per
+                // block, then the exact pair terms of all hits (from hi + lo) are
+                // summed in list order in a single loop, so a warp's divergent
+                // iterations are its largest total hit count, not a sum of
+                // per-block maxima
                 const uint32_t l0 = s_vox_loff[v], l1 = s_vox_loff[v + 1];
-                for (uint32_t cb = l0; cb < l1; cb += 32u) {
-                    const uint32_t nc = min(32u, l1 - cb);
-                    uint32_t hits = 0;
+                for (uint32_t cb = l0; cb < l1; cb += 96u) {
+                    uint32_t m[3] = {0u, 0u, 0u};
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const uint32_t c0 = cb + 32u * (uint32_t)b;
+                        const uint32_t nc = c0 < l1 ? min(32u, l1 - c0) : 0u;
 #pragma unroll 8
-                    for (uint32_t k = 0; k < nc; ++k) {
-                        const float4 pj = sp[clist[cb + k]];
-                        hits |= (candidate_hit(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, A, pj.w, cut_i) ? 1u : 0u) << k;
+                        for (uint32_t k2 = 0; k2 < nc; ++k2) {
+                            const float4 pj = sp[clist[c0 + k2]];
+                            m[b] |= (candidate_hit(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, A, pj.w, cut_i) ? 1u : 0u)
+                                    << k2;
+                        }
                     }
-                    while (hits) {
-                        const uint32_t k = (uint32_t)(__ffs(hits) - 1);
-                        hits &= hits - 1u;
-                        const uint32_t jj = clist[cb + k];
+                    while (m[0] | m[1] | m[2]) {
+                        const int b = m[0] ? 0 : (m[1] ? 1 : 2);
+                        const uint32_t mb = b == 0 ? m[0] : (b == 1 ? m[1] : m[2]);
+                        const uint32_t k2 = (uint32_t)(__ffs(mb) - 1);
+                        const uint32_t rest = mb & (mb - 1u);
+                        if (b == 0) m[0] = rest; else if (b == 1) m[1] = rest; else m[2] = rest;
+                        const uint32_t jj = clist[cb + 32u * (uint32_t)b + k2];
                         const float4 p2 = sp[jj];
                         const float4 q2 = sq[jj];
                         const float4 l2 = record_lo(p2, q2, g.qs);
