@@ -485,8 +485,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
         if (rc == MECH_OK) rc = h->alloc(&b.vp64, 3 * np);
         if (rc == MECH_OK) rc = h->alloc(&b.vpf, 3 * np);
         if (rc == MECH_OK) rc = h->alloc(&b.id, np);
-        if (rc == MECH_OK) rc = h->alloc(&b.recp, np);
-        if (rc == MECH_OK) rc = h->alloc(&b.recq, np);
+        if (rc == MECH_OK) rc = h->alloc(&b.rec, 2 * np);
     }
     if (rc == MECH_OK) rc = h->alloc(&h->d_R64, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_ccr64, np);
@@ -506,11 +505,11 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
 
     // caller order = initial state order; parameters and ids
     std::vector<uint32_t> ids(n);
-    std::vector<float4> recp(n), recq(n);
+    std::vector<float4> rec(2 * n);
     for (int64_t i = 0; i < n; ++i) {
         ids[i] = (uint32_t)i;
         // radius as FP32 + 16-bit residual in units of ulp(R) / 2^15 (upper half
-        // of recq.w); position residual fields start at zero (0x8000)
+        // of the second float4); position residual fields start at zero (0x8000)
         const float Rf = (float)R[i];
         int e2 = 0;
         std::frexp(Rf, &e2);  // Rf = m 2^e2, m in [0.5, 1): ulp = 2^(e2 - 24)
@@ -521,8 +520,8 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
         const uint32_t wxy = 0x80008000u;
         std::memcpy(&wzf, &wzr, 4);
         std::memcpy(&wxyf, &wxy, 4);
-        recp[i] = make_float4(0.f, 0.f, 0.f, Rf);
-        recq[i] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), wxyf, wzf);
+        rec[2 * i] = make_float4(0.f, 0.f, 0.f, Rf);
+        rec[2 * i + 1] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), wxyf, wzf);
     }
     cudaStream_t s = h->stream;
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -530,8 +529,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     };
     cudaError_t ce = cudaSuccess;
     if (ce == cudaSuccess) ce = up(h->st[0].id, ids.data(), n * 4);
-    if (ce == cudaSuccess) ce = up(h->st[0].recp, recp.data(), n * sizeof(float4));
-    if (ce == cudaSuccess) ce = up(h->st[0].recq, recq.data(), n * sizeof(float4));
+    if (ce == cudaSuccess) ce = up(h->st[0].rec, rec.data(), 2 * n * sizeof(float4));
     if (ce == cudaSuccess) ce = up(h->d_R64, R, n * 8);
     if (ce == cudaSuccess) ce = up(h->d_ccr64, ccr, n * 8);
     if (ce == cudaSuccess) ce = up(h->d_cca64, cca, n * 8);

@@ -234,12 +234,12 @@ __global__ void k_canon(const StepArgs a) {
             }
         }
         // radius, its residual and the coefficients travel with the record
-        const float4 pa = a.A.recp[src];
-        const float4 qa = a.A.recq[src];
+        const float4 pa = a.A.rec[2 * (size_t)src];
+        const float4 qa = a.A.rec[2 * (size_t)src + 1];
         const uint32_t wxy = fix16(lo[0] * g.inv_q) | (fix16(lo[1] * g.inv_q) << 16);
         const uint32_t wzr = fix16(lo[2] * g.inv_q) | (__float_as_uint(qa.w) & 0xFFFF0000u);
-        a.B.recp[f] = make_float4(hi[0], hi[1], hi[2], pa.w);
-        a.B.recq[f] = make_float4(qa.x, qa.y, __uint_as_float(wxy), __uint_as_float(wzr));
+        a.B.rec[2 * (size_t)f] = make_float4(hi[0], hi[1], hi[2], pa.w);
+        a.B.rec[2 * (size_t)f + 1] = make_float4(qa.x, qa.y, __uint_as_float(wxy), __uint_as_float(wzr));
     }
 }
 

@@ -250,8 +250,8 @@ __device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, 
 // a cell with few or no neighbours costs one round of memory latency, not nine.
 // Candidates are tested on the hi parts; a pair that passes is evaluated from
 // hi + lo.
-__device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, const float4 pi,
-                                              const float4 qi, Acc3& acc) {
+__device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, uint32_t q,
+                                              const float4 pi, const float4 qi, Acc3& acc) {
     const float A = a.A_f;
     const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
     const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
@@ -281,10 +281,10 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
             if (!((rb >> (jx - jx0)) & 1u)) continue;
             const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
             for (uint32_t j = s; j < e; ++j) {
-                const float4 pj = a.B.recp[j];
+                const float4 pj = a.B.rec[2 * (size_t)j];
                 const float hx = pi.x - pj.x, hy = pi.y - pj.y, hz = pi.z - pj.z;
-                if (candidate_hit(hx, hy, hz, A, pj.w, cut_i)) {
-                    const float4 qj = a.B.recq[j];
+                if (j != q && candidate_hit(hx, hy, hz, A, pj.w, cut_i)) {
+                    const float4 qj = a.B.rec[2 * (size_t)j + 1];
                     const float4 lj = record_lo(pj, qj, g.qs);
                     pair_term(hx, hy, hz, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w, li.w + lj.w, qi.x, qi.y,
                               qj.x, qj.y, A, acc);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(a.vkey_s[q], g);
             Acc3 acc;
-            velocity_walk(a, g, c, a.B.recp[q], a.B.recq[q], acc);
+            velocity_walk(a, g, c, q, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
             int nix, niy, niz;
             nkey = ab2_epilogue<MODE>(a, g, q, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
@@ -394,14 +394,14 @@ __global__ void k_sparse_list(const StepArgs a) {
 //   1. halo row table: for each (y, z) row of the halo (one voxel around the
 //      tile), the global start of its run of force records and the voxel
 //      boundaries inside it;
-//   2. TMA: one bulk copy per row and array (positions, coefficients) into
+//   2. TMA: one bulk copy per row (its 32-byte records are contiguous) into
 //      shared memory, completion on an mbarrier (bounded wait);
-//   4. for every core voxel, the shared-memory indices of its 27-voxel
+//   3. for every core voxel, the shared-memory indices of its 27-voxel
 //      neighbourhood (9 contiguous row ranges) are written into one list;
-//   5. one thread per target cell scans its voxel's list 32 candidates at a
-//      time: a branch-free conservative cutoff test builds a hit mask, then the
-//      exact pair terms of the hits are summed in list order; then AB2 and the
-//      next-step histogram.
+//   4. one thread per target cell scans its voxel's list in blocks of 32
+//      candidates: a branch-free cutoff test on the hi parts builds a hit
+//      mask per block, then the exact pair terms of the hits are summed in
+//      list order; then AB2 and the next-step histograms.
 // A tile whose halo or lists do not fit clears its dense flag and leaves its
 // cells to the thread-per-cell kernel, which runs after this one.
 
@@ -433,9 +433,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
     constexpr int HX = 6, NB = HX + 1, NROW = HX * HX, NVOX = 64;
     extern __shared__ __align__(128) unsigned char dsm[];
-    float4* sp = reinterpret_cast<float4*>(dsm);          // hi positions + radius
-    float4* sq = sp + kTCap;                              // coefficient square roots + residuals
-    uint16_t* clist = reinterpret_cast<uint16_t*>(sq + kTCap);   // per-voxel candidate lists
+    float4* srec = reinterpret_cast<float4*>(dsm);        // staged force records (two float4 each)
+    uint16_t* clist = reinterpret_cast<uint16_t*>(srec + 2 * kTCap);   // per-voxel candidate lists
     __shared__ uint32_t s_row_gs[NROW];
     __shared__ uint32_t s_row_off[NROW + 1];
     __shared__ uint32_t s_row_vb[NROW][NB];
@@ -507,12 +506,11 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
             if (tid == 0)
                 mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4) +
                                                   ((a.fault & kFaultTileWait) ? 16u : 0u));
-            if (len) {
-                bulk_g2s(&sp[s_row_off[rr]], &a.B.recp[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
-                bulk_g2s(&sq[s_row_off[rr]], &a.B.recq[s_row_gs[rr]], len * (uint32_t)sizeof(float4), &s_bar);
-            }
+            if (len)
+                bulk_g2s(&srec[2 * s_row_off[rr]], &a.B.rec[2 * (size_t)s_row_gs[rr]],
+                         len * 2u * (uint32_t)sizeof(float4), &s_bar);
         } else if (tid >= 64 && tid < 64 + NVOX) {
-            // 4a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
+            // 3a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
             const int v = tid - 64;
             const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
             uint32_t len = 0;
@@ -538,7 +536,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
                 s_vox_toff[NVOX] = t_total;
             }
         }
-        // 3. wait for the halo
+        // 2b. wait for the halo
         if (!mbar_wait_bounded(&s_bar, phase, a.wait_ns)) s_flag = 1;
         phase ^= 1u;
         __syncthreads();
@@ -552,7 +550,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
             __syncthreads();
             continue;
         }
-        // 4b. candidate index lists, one (voxel, neighbour row) pair per thread,
+        // 3b. candidate index lists, one (voxel, neighbour row) pair per thread,
         // and the core voxel of every target
         for (int w = tid; w < NVOX * 9; w += kTT) {
             const int v = w / 9, p = w - v * 9;
@@ -565,7 +563,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
                 for (uint32_t t = s_vox_toff[v]; t < s_vox_toff[v + 1]; ++t) s_tvox[t] = (uint8_t)v;
         }
         __syncthreads();
-        // 5. one thread per target
+        // 4. one thread per target
         const uint32_t T = s_vox_toff[NVOX];
         for (uint32_t t0 = (uint32_t)warp * 32u; t0 < T; t0 += kTT) {
             const uint32_t t = t0 + lane;
@@ -579,8 +577,8 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
                 const uint32_t in_row = s_row_vb[rr][cx + 1] + k;
                 q = s_row_gs[rr] + in_row;
                 const uint32_t si = s_row_off[rr] + in_row;
-                const float4 pi = sp[si];
-                const float4 qi = sq[si];
+                const float4 pi = srec[2 * si];
+                const float4 qi = srec[2 * si + 1];
                 const float4 li = record_lo(pi, qi, g.qs);
                 const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
                 Acc3 acc;
@@ -600,7 +598,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
                         const uint32_t nc = c0 < l1 ? min(32u, l1 - c0) : 0u;
 #pragma unroll 8
                         for (uint32_t k2 = 0; k2 < nc; ++k2) {
-                            const float4 pj = sp[clist[c0 + k2]];
+                            const float4 pj = srec[2 * (uint32_t)clist[c0 + k2]];
                             m[b] |= (candidate_hit(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, A, pj.w, cut_i) ? 1u : 0u)
                                     << k2;
                         }
@@ -612,8 +610,8 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
                         const uint32_t rest = mb & (mb - 1u);
                         if (b == 0) m[0] = rest; else if (b == 1) m[1] = rest; else m[2] = rest;
                         const uint32_t jj = clist[cb + 32u * (uint32_t)b + k2];
-                        const float4 p2 = sp[jj];
-                        const float4 q2 = sq[jj];
+                        const float4 p2 = srec[2 * jj];
+                        const float4 q2 = srec[2 * jj + 1];
                         const float4 l2 = record_lo(p2, q2, g.qs);
                         pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y, li.z - l2.z, pi.w,
                                   p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, A, acc);
@@ -650,7 +648,7 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(a.vkey_s[q], g);
-            const float4 pi = a.B.recp[q];
+            const float4 pi = a.B.rec[2 * (size_t)q];
             const uint32_t src = a.perm[q];
             const uint32_t idi = a.A.id[src];
             const double xi = a.A.pos64[src], yi = a.A.pos64[np + src], zi = a.A.pos64[2 * np + src];
@@ -671,7 +669,7 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
                         const uint32_t e = a.start[row + jx + 1];
                         for (uint32_t j = s; j < e; ++j) {
                             if (j == q) continue;
-                            const float4 pj = a.B.recp[j];
+                            const float4 pj = a.B.rec[2 * (size_t)j];
                             const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
                             const float d2f = rx * rx + ry * ry + rz * rz;
                             const float cut = fmaf(A, pj.w, cut_i);

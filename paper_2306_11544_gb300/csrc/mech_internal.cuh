@@ -10,14 +10,16 @@
 //       vp64   [3][npad] double   previous velocity (FP64 mode)
 //       vpf    [3][npad] float    previous velocity (mixed modes)
 //       id     [n]       u32      caller index of the cell
-//       recp   [n]       float4   {x_hi, y_hi, z_hi, R}: position relative to
-//                                 the replicate's grid centre as a hi part on
-//                                 a power-of-two grid q, and the radius (FP32)
-//       recq   [n]       float4   {sqrt(ccr), sqrt(cca), lo_xy, lo_zr}: the
-//                                 coefficient square roots, then four 16-bit
-//                                 fixed-point residuals: x_lo, y_lo, z_lo in
-//                                 units of q / 2^15 and R - (float)R in units
-//                                 of ulp(R) / 2^15
+//       rec    [2n]      float4   force record of cell i, 32 contiguous bytes:
+//                                 rec[2i]   = {x_hi, y_hi, z_hi, R}: position
+//                                 relative to the replicate's grid centre as a
+//                                 hi part on a power-of-two grid q, and the
+//                                 radius (FP32);
+//                                 rec[2i+1] = {sqrt(ccr), sqrt(cca), lo_xy,
+//                                 lo_zr}: the coefficient square roots, then
+//                                 four 16-bit fixed-point residuals: x_lo,
+//                                 y_lo, z_lo in units of q / 2^15 and
+//                                 R - (float)R in units of ulp(R) / 2^15
 //     The canonicalisation pass also copies each cell's state (positions,
 //     compensation, previous velocity) into B order, so the force kernels
 //     read and update their own cells contiguously.
@@ -130,8 +132,7 @@ struct StateBuf {
     double* vp64;
     float* vpf;
     uint32_t* id;
-    float4* recp;
-    float4* recq;
+    float4* rec;       // force records, two float4 per cell (see the layout above)
 };
 
 struct StepArgs {
