@@ -36,6 +36,19 @@ METRIC = "mechanics cell-steps/s (bin+force+AB2), batched vs plain, at <=1e-3 um
 UNIT = "cell-steps/s"
 # Algorithmic bytes (compulsory HBM traffic) of the fixed byte model.
 FORCE_BYTES_PER_CELL = 84      # read x 24 + params 12 + v_prev 12, write x 24 + v 12
+# Algorithmic FP32 operations of the force phase (definition of the method,
+# counted per operation; a fused multiply-add is two): a neighbour test
+# (difference 3, squares and sum 5, compare 1), an interacting ordered pair
+# (sqrt 1; S, A S, d/(A S), 1 - . 4; square and coefficient 4; d/S and 1 - . 2,
+# square and coefficient 4; c_r - c_a 1; /d 1; times r 3; accumulate 3) and the
+# AB2 update of a cell (5 per component).
+OPS_PER_CANDIDATE = 9
+OPS_PER_ORDERED_PAIR = 23
+OPS_PER_CELL_AB2 = 15
+# FP32 peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 ops
+# (fused multiply-add) x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 STEP_BYTES_PER_CELL = 228      # key+hist 28, scatter 116, force+AB2 84
 STEP_BYTES_PER_VOXEL = 20      # histogram zero/atomics 12, scan 8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -448,6 +461,7 @@ def main():
         e2e = {"value": total_cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
                "d2h_bytes_per_step": 24 * n, "steps": args.e2e_steps,
                "path": "mech_write_positions (pinned host) -> mech_step(1) -> mech_read_positions (pinned host)"}
+    stats = m.pair_stats() if profile else None  # (candidates, interacting pairs) of the final positions
     m.close()
 
     if rank != 0:
@@ -458,18 +472,34 @@ def main():
     peak, peak_kind = hbm_peak()
     roof = None
     if profile and psteps:
+        # the force phase (velocity + AB2 kernels) dominates the step; its
+        # bound is instruction issue, so the roofline is the FP32 one, with the
+        # method's operation count from the neighbour statistics of the run
         t_force = (phases["classify"] + phases["tiles"] + phases["cells"]) / psteps * 1e-3
-        ach = FORCE_BYTES_PER_CELL * n / t_force / 1e9
+        cand, pairs = stats
+        ops = OPS_PER_CANDIDATE * cand + OPS_PER_ORDERED_PAIR * 2 * pairs + OPS_PER_CELL_AB2 * n
+        ach = ops / t_force / 1e12
         tr = force_traffic()
-        kern = "k_force_fp64" if args.mode == "fp64" else "k_tile_classify + k_force_tile + k_force_cells"
-        roof = {"bound": "hbm", "kernel": kern,
-                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "bytes_per_launch": FORCE_BYTES_PER_CELL * n,
-                "bytes_model": f"{FORCE_BYTES_PER_CELL} B/cell (x, params, v_prev in; x, v out)",
+        kern = ("k_force_fp64" if args.mode == "fp64"
+                else "force phase: k_tile_classify + k_force_tile + k_sparse_list + k_force_cells")
+        bytes_alg = FORCE_BYTES_PER_CELL * n
+        alu_peak, alu_kind = ((FP64_PEAK_TFLOPS, "nominal FP64 rate of the part") if args.mode == "fp64" else
+                              (FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"))
+        roof = {"bound": "alu", "kernel": kern,
+                "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "peak_kind": alu_kind,
+                "ops_per_launch": ops,
+                "ops_model": f"{OPS_PER_CANDIDATE}/neighbour test x {cand} + {OPS_PER_ORDERED_PAIR}/ordered pair x "
+                             f"{2 * pairs} + {OPS_PER_CELL_AB2}/cell AB2 x {n}",
+                "candidates": cand, "interacting_pairs": pairs,
                 "launch_ms": 1e3 * t_force,
                 "traffic": None if tr is None else tr.get("dram_bytes_per_cell", 0) * n,
-                "traffic_source": None if tr is None else tr.get("source")}
+                "traffic_source": None if tr is None else tr.get("source"),
+                "hbm_view": {"bytes_per_launch": bytes_alg,
+                             "bytes_model": f"{FORCE_BYTES_PER_CELL} B/cell (x, params, v_prev in; x, v out)",
+                             "achieved": bytes_alg / t_force / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": bytes_alg / t_force / 1e9 / peak,
+                             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}}
     # algorithmic model on the workload's own voxel grid (the internal grid the
     # autotuner may pick is a performance choice, not work of the problem)
     reps = [wl] if not batched else wl.reps

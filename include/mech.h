@@ -207,6 +207,22 @@ MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, 
 MECH_API int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order);
 
 /*
+ * Neighbour statistics of the current positions (Sec. 5.4: each cell's
+ * velocity is gathered from the cells of its 27 neighbouring mechanics
+ * voxels; a neighbour contributes when 0 < d < A (R_i + R_j)):
+ *   candidates: ordered pairs (i, j != i) with j in one of the 27 voxels
+ *               around i's voxel on the internal grid the step uses
+ *               (mech_set_internal_voxel), i.e. the neighbour tests one step
+ *               performs;
+ *   pairs:      unordered interacting pairs {i, j}, 0 < d < A (R_i + R_j),
+ *               decided in FP64 from the current positions (x_hi - c in
+ *               MECH_MIXED_KAHAN mode) with the same operations as the
+ *               definition (no contraction, IEEE square root).
+ * Either output may be NULL.  Synchronous; does not advance the state.
+ */
+MECH_API int mech_pair_stats(mech_t* h, int64_t* candidates, int64_t* pairs);
+
+/*
  * Binning without allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they call it --
  * code whose device memory is already entirely reserved by another allocator

@@ -83,6 +83,7 @@ struct mech {
     uint32_t* d_ndense = nullptr;
     uint32_t* d_slist = nullptr;
     uint32_t* d_nsparse = nullptr;
+    unsigned long long* d_stats = nullptr;  // mech_pair_stats counters
     // state
     StateBuf st[2] = {};
     int cur = 0;
@@ -493,6 +494,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (rc == MECH_OK) rc = h->alloc(&h->d_key, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_slist, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_nsparse, 1);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_stats, 2);
     if (rc == MECH_OK) rc = h->alloc(&h->d_vkey_s, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_perm, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_tmp, np);
@@ -907,6 +909,33 @@ int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, 
     return check_err_flag(h);
 }
 
+int mech_pair_stats(mech_t* h, int64_t* candidates, int64_t* pairs) {
+    MECH_TRY(ready(h));
+    if (candidates) *candidates = 0;
+    if (pairs) *pairs = 0;
+    if (h->n == 0) return MECH_OK;
+    if (h->poisoned)
+        return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
+    // FP64 positions in caller order, then a binning pass into the B buffers
+    StepArgs a = h->args(h->cur, 1);
+    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->stream));
+    h->keys_valid = false;
+    MECH_TRY(ensure_keys(h));
+    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, h->d_occ, h->stream));
+    CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
+    CUDA_TRY(launch_canon(a, h->elem_grid, h->stream));
+    h->keys_valid = false;  // the scatter counted the histogram down
+    CUDA_TRY(cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream));
+    CUDA_TRY(launch_pair_stats(a, h->d_io, h->d_stats, h->sms * 8, h->stream));
+    unsigned long long c[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(c, h->d_stats, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    MECH_TRY(check_err_flag(h));
+    if (candidates) *candidates = (int64_t)c[0];
+    if (pairs) *pairs = (int64_t)(c[1] / 2);
+    return MECH_OK;
+}
+
 int mech_debug_inject(mech_t* h, int32_t fault) {
     if (fault == MECH_FAULT_ALLOC) {
         g_fault_alloc.store(1);
@@ -936,7 +965,7 @@ int mech_info(mech_t* h, mech_info_t* out) {
         for (int d = 0; d < 3; ++d) out->dims[d] = h->grids[0].n[d];
     out->voxel = voxel_of(h);
     out->step = h->step;
-    out->launches_per_step = h->n > 0 ? ((h->mode != kFP64 && h->use_tiles) ? 8 : 7) : 0;
+    out->launches_per_step = h->n > 0 ? ((h->mode != kFP64 && h->use_tiles) ? 9 : 7) : 0;
     out->graph_steps = h->graph_steps;
     out->device_bytes = (int64_t)h->dev_bytes;
     return MECH_OK;

@@ -731,6 +731,56 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
     }
 }
 
+// ------------------------------------------------------ pair stats ----
+// One thread per cell of the voxel order in B: counts its candidates (cells of
+// the 27 neighbour voxels, itself excluded) and its interacting neighbours,
+// decided in FP64 from caller-order positions exactly as the definition does.
+__global__ void __launch_bounds__(kCellBlock) k_pair_stats(const StepArgs a, const double* __restrict__ xyz,
+                                                          unsigned long long* __restrict__ out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned long long cand = 0, hits = 0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const int r = rep_of_cell(a.grids, a.nrep, q);
+        const GridDev& g = a.grids[r];
+        const Cell3 c = decode(a.vkey_s[q], g);
+        const uint32_t idi = a.B.id[q];
+        const double xi = xyz[3 * (size_t)idi], yi = xyz[3 * (size_t)idi + 1], zi = xyz[3 * (size_t)idi + 2];
+        const double Ri = a.R64[idi];
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int jz = c.iz + dz;
+            if (jz < 0 || jz >= g.n[2]) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int jy = c.iy + dy;
+                if (jy < 0 || jy >= g.n[1]) continue;
+                const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
+                const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
+                const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
+                const uint32_t s = a.start[row + jx0], e = a.start[row + jx1 + 1];
+                for (uint32_t j = s; j < e; ++j) {
+                    if (j == q) continue;
+                    ++cand;
+                    const uint32_t idj = a.B.id[j];
+                    const double dx = __dsub_rn(xi, xyz[3 * (size_t)idj]);
+                    const double dy2 = __dsub_rn(yi, xyz[3 * (size_t)idj + 1]);
+                    const double dz2 = __dsub_rn(zi, xyz[3 * (size_t)idj + 2]);
+                    const double d = __dsqrt_rn(
+                        __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2)), __dmul_rn(dz2, dz2)));
+                    if (d > 0.0 && d < __dmul_rn(a.A_d, __dadd_rn(Ri, a.R64[idj]))) ++hits;
+                }
+            }
+        }
+    }
+    // warp sums, one atomic per warp and counter
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_down_sync(0xFFFFFFFFu, cand, o);
+        hits += __shfl_down_sync(0xFFFFFFFFu, hits, o);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        atomicAdd(&out[0], cand);
+        atomicAdd(&out[1], hits);
+    }
+}
+
 // ---- tile kernel launch ----
 template <int MODE>
 cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
@@ -786,6 +836,13 @@ cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
     k_sparse_list<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_stats(const StepArgs& a, const double* xyz, unsigned long long* out, int grid,
+                              cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_pair_stats<<<grid, kCellBlock, 0, s>>>(a, xyz, out);
     return cudaGetLastError();
 }
 

@@ -204,6 +204,11 @@ int record_error(int code, const std::string& msg);
 cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s);
+// Neighbour statistics of the voxel order in a.B (after a binning pass) from
+// FP64 positions in caller order: out[0] += candidates, out[1] += ordered
+// interacting pairs.
+cudaError_t launch_pair_stats(const StepArgs& a, const double* xyz, unsigned long long* out, int grid,
+                              cudaStream_t s);
 cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStream_t s);
 int force_max_blocks_per_sm(int mode, int block);
 int tile_kernel_grid(const StepArgs& a, int sms);

@@ -43,7 +43,7 @@ EXPORTS = [
     "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
-    "mech_load_state", "mech_debug_bins", "mech_bin_noalloc", "mech_debug_inject", "mech_info", "mech_grid",
+    "mech_load_state", "mech_debug_bins", "mech_pair_stats", "mech_bin_noalloc", "mech_debug_inject", "mech_info", "mech_grid",
     "mech_destroy",
 ]
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
             "mech_read_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_load_state": ([_P, _P, _P, _P, ctypes.c_int64], ctypes.c_int),
             "mech_debug_bins": ([_P, _P, _P, _P, _P], ctypes.c_int),
+            "mech_pair_stats": ([_P, _P, _P], ctypes.c_int),
             "mech_bin_noalloc": ([ctypes.c_int64, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P], ctypes.c_int),
             "mech_debug_inject": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_info": ([_P, _P], ctypes.c_int),
@@ -292,6 +293,14 @@ def mech_grid(h, rep):
     return lo, dims, int(vb.value)
 
 
+def mech_pair_stats(h):
+    """(candidates, interacting pairs) of the current positions."""
+    c = ctypes.c_int64(0)
+    p = ctypes.c_int64(0)
+    _check(load_library().mech_pair_stats(h, ctypes.byref(c), ctypes.byref(p)), "mech_pair_stats")
+    return int(c.value), int(p.value)
+
+
 def mech_debug_bins(h, n):
     V = mech_info(h)["n_voxels"]
     key = np.empty(n, dtype=np.uint32)
@@ -421,6 +430,10 @@ class Mech:
 
     def bins(self):
         return mech_debug_bins(self.h, self.n)
+
+    def pair_stats(self):
+        """(candidate pairs tested by one step, interacting pairs) of the current positions."""
+        return mech_pair_stats(self.h)
 
     def info(self):
         return mech_info(self.h)

@@ -335,3 +335,38 @@ def test_autotuner_restores_state_and_stays_correct():
         v = m.velocities()
     vref = oracle.velocities(x, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
     assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+
+
+def candidates_from_bins(m):
+    """Ordered candidate pairs of the 27-voxel stencil, from the binning itself."""
+    key, count, _, _ = m.bins()
+    _, dims, _ = m.grid(0)
+    dims = dims.astype(np.int64)
+    k = key.astype(np.int64)
+    ix, iy, iz = k % dims[0], (k // dims[0]) % dims[1], k // (dims[0] * dims[1])
+    total = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                jx, jy, jz = ix + dx, iy + dy, iz + dz
+                ok = (jx >= 0) & (jx < dims[0]) & (jy >= 0) & (jy < dims[1]) & (jz >= 0) & (jz < dims[2])
+                vk = jx[ok] + dims[0] * (jy[ok] + dims[1] * jz[ok])
+                total += int(count[vk].astype(np.int64).sum())
+    return total - key.size
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name,voxel", [("spheroid_2k", None), ("clustered_small", "min")])
+def test_pair_stats_match_oracle(name, voxel, mode):
+    """Interacting pairs are the oracle's pair set (bit-exact count, FP64
+    decision); candidates are the 27-voxel stencil of the binning."""
+    pop = synth.spheroid_2k(seed=21) if name == "spheroid_2k" else synth.clustered_20m(seed=22, scale=0.002)
+    hv = 2 * pop.A * pop.R.max() * (1 + 1e-5) if voxel == "min" else None
+    with H.make(pop, mode, voxel=hv) as m:
+        m.step(3)
+        cand, pairs = m.pair_stats()
+        x = m.positions()
+        assert cand == candidates_from_bins(m)
+    pref = oracle.pairs(x, pop.R, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert pairs == pref.shape[0]
+    assert pairs > 0 and cand > 2 * pairs
