@@ -81,7 +81,7 @@ struct mech {
     uint8_t* d_tdense = nullptr;
     uint32_t* d_tlist = nullptr;
     uint32_t* d_ndense = nullptr;
-    uint32_t* d_slist = nullptr;
+    uint2* d_slist = nullptr;
     uint32_t* d_nsparse = nullptr;
     unsigned long long* d_stats = nullptr;  // mech_pair_stats counters
     // state

@@ -189,30 +189,55 @@ __device__ __forceinline__ bool candidate_hit(float hx, float hy, float hz, floa
     return hx * hx + hy * hy + hz * hz < c * c;
 }
 
-// AB2 update of cell q (B order).  Its state was copied into B order by the
-// canonicalisation pass; it is read and updated in place.  Returns the next
-// step's voxel key and its voxel coordinates.
+// State of cell q (B order) that its AB2 update reads: previous velocity and
+// position (FP64, or FP32 x_hi with its compensation).  Its state was copied
+// into B order by the canonicalisation pass.
 template <int MODE>
-__device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, float ax, float ay,
-                                                 float az, int& nix, int& niy, int& niz) {
+struct CellState {
+    float vp[3];
+    float xh[3], cc[3];  // Kahan mode
+    double x[3];         // FP64-position mode
+};
+
+template <int MODE>
+__device__ __forceinline__ CellState<MODE> load_cell_state(const StepArgs& a, uint32_t q) {
+    const size_t np = a.npad;
+    CellState<MODE> st;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.vp[d] = a.B.vpf[d * np + q];
+        if (MODE == kMixedFP64Pos) {
+            st.x[d] = a.B.pos64[d * np + q];
+        } else {
+            st.xh[d] = a.B.posf[d * np + q];
+            st.cc[d] = a.B.comp[d * np + q];
+        }
+    }
+    return st;
+}
+
+// AB2 update of cell q (B order) in place; returns the next step's voxel key
+// and its voxel coordinates.
+template <int MODE>
+__device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& g, uint32_t q,
+                                              const CellState<MODE>& st, float ax, float ay, float az, int& nix,
+                                              int& niy, int& niz) {
     const size_t np = a.npad;
     const float v[3] = {ax, ay, az};
     bool finite = true;
     float xf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const float vp = a.B.vpf[d * np + q];
-        const float inc = a.dt_f * (1.5f * v[d] - 0.5f * vp);
+        const float inc = a.dt_f * (1.5f * v[d] - 0.5f * st.vp[d]);
         if (MODE == kMixedFP64Pos) {
-            const double x = a.B.pos64[d * np + q];
-            const double xn = a.integrate ? __dadd_rn(x, (double)inc) : x;
+            const double xn = a.integrate ? __dadd_rn(st.x[d], (double)inc) : st.x[d];
             if (a.integrate) a.B.pos64[d * np + q] = xn;
             xf[d] = __double2float_rn(xn);
             finite = finite && isfinite(xn);
         } else {
-            float xh = a.B.posf[d * np + q];
+            float xh = st.xh[d];
             if (a.integrate) {
-                float cc = a.B.comp[d * np + q];
+                float cc = st.cc[d];
                 const float y = __fsub_rn(inc, cc);
                 const float t = __fadd_rn(xh, y);
                 cc = __fsub_rn(__fsub_rn(t, xh), y);
@@ -232,6 +257,13 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
     niy = axis_index_f32(xf[1], g.lo_f[1], g.inv_h_f, g.n[1]);
     niz = axis_index_f32(xf[2], g.lo_f[2], g.inv_h_f, g.n[2]);
     return g.vbase + (uint32_t)nix + (uint32_t)g.n[0] * ((uint32_t)niy + (uint32_t)g.n[1] * (uint32_t)niz);
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, float ax, float ay,
+                                                 float az, int& nix, int& niy, int& niz) {
+    const CellState<MODE> st = load_cell_state<MODE>(a, q);
+    return ab2_apply<MODE>(a, g, q, st, ax, ay, az, nix, niy, niz);
 }
 
 // Next-step histograms (voxels, tiles) and key of cell q; all 32 lanes call it.
@@ -308,14 +340,23 @@ __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
         const bool valid = idx < total;
         uint32_t q = 0, nkey = 0, ntile = 0;
         if (valid) {
-            q = a.use_tiles ? a.slist[idx] : idx;
+            uint32_t key;
+            if (a.use_tiles) {
+                const uint2 e = a.slist[idx];
+                q = e.x;
+                key = e.y;
+            } else {
+                q = idx;
+                key = a.vkey_s[q];
+            }
+            const CellState<MODE> st = load_cell_state<MODE>(a, q);  // issued before the walk
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
-            const Cell3 c = decode(a.vkey_s[q], g);
+            const Cell3 c = decode(key, g);
             Acc3 acc;
             velocity_walk(a, g, c, q, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
             int nix, niy, niz;
-            nkey = ab2_epilogue<MODE>(a, g, q, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
+            nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
         }
         next_step_counts(a, q, nkey, ntile, valid);
@@ -366,8 +407,9 @@ __global__ void k_tile_classify(const StepArgs a) {
 }
 
 // ------------------------------------------------------ sparse list ----
-// After the tile kernel (which may hand tiles back): B positions of every cell
-// whose tile is not dense, in runs of a warp's 32 consecutive cells.
+// After the tile kernel (which may hand tiles back): B position and voxel key
+// of every cell whose tile is not dense, in runs of a warp's 32 consecutive
+// cells.
 __global__ void k_sparse_list(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -375,17 +417,19 @@ __global__ void k_sparse_list(const StepArgs a) {
     for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
         const uint32_t q = base + lane;
         bool sparse = false;
+        uint32_t k = 0;
         if (q < a.n) {
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
-            const Cell3 c = decode(a.vkey_s[q], g);
+            k = a.vkey_s[q];
+            const Cell3 c = decode(k, g);
             sparse = !a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)];
         }
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, sparse);
         uint32_t off = 0;
         if (lane == 0 && m) off = atomicAdd(a.nsparse, (uint32_t)__popc(m));
         off = __shfl_sync(0xFFFFFFFFu, off, 0);
-        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = q;
+        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = make_uint2(q, k);
     }
 }
 
