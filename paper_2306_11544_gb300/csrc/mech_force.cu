@@ -364,13 +364,13 @@ __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
 }
 
 // A tile is processed by the tile kernel only when its whole halo lies inside
-// the grid (1 <= b and 4 b + 4 <= n - 1 on every axis): the kernel's shape is
-// then fixed (6 x 6 halo rows of 6 voxels around 4 x 4 x 4 core voxels) and its
-// index arithmetic compiles to constants.  Tiles at the grid faces go to the
-// thread-per-cell kernel.
-__device__ __forceinline__ bool tile_interior(const GridDev& g, int bx, int by, int bz) {
+// the grid (1 <= b and T b + T <= n - 1 on every axis, T the tile's extent):
+// the kernel's shape is then fixed (6 x (TZ + 2) halo rows of 6 voxels around
+// 4 x 4 x TZ core voxels) and its index arithmetic compiles to constants.
+// Tiles at the grid faces go to the thread-per-cell kernel.
+__device__ __forceinline__ bool tile_interior(const GridDev& g, int bx, int by, int bz, int tz) {
     return bx >= 1 && by >= 1 && bz >= 1 && 4 * bx + 4 <= g.n[0] - 1 && 4 * by + 4 <= g.n[1] - 1 &&
-           4 * bz + 4 <= g.n[2] - 1;
+           tz * bz + tz <= g.n[2] - 1;
 }
 
 // ----------------------------------------------------- tile classify ----
@@ -393,7 +393,7 @@ __global__ void k_tile_classify(const StepArgs a) {
                 const uint32_t lt = t - g.tbase;
                 const uint32_t rest = lt / (uint32_t)g.nt[0];
                 dense = tile_interior(g, (int)(lt % (uint32_t)g.nt[0]), (int)(rest % (uint32_t)g.nt[1]),
-                                      (int)(rest / (uint32_t)g.nt[1]));
+                                      (int)(rest / (uint32_t)g.nt[1]), 1 << a.ltz);
             }
             a.tdense[t] = dense ? 1 : 0;
             a.tcount_nxt[t] = 0u;
@@ -468,14 +468,25 @@ __device__ __forceinline__ uint32_t warp_scan_inplace(uint32_t* v, int n) {
     return carry;
 }
 
-constexpr int kTT = 160;          // threads per tile CTA (about one target each)
-constexpr int kTCap = 640;        // staged halo records per tile (a dense core tile holds ~490)
-constexpr int kTListCap = 5120;   // candidate-list entries per tile
-constexpr size_t kTileDynSmem = (size_t)kTCap * 2 * sizeof(float4) + (size_t)kTListCap * 2;
+// Tile of 4 x 4 x TZ voxels (TZ = 2^LZ, 4 or 8): threads per CTA (about one
+// per target), CTAs per SM, staged halo records (a dense core 4x4x4 tile holds
+// ~490 of 216 halo voxels) and candidate-list entries per tile.
+template <int LZ>
+struct TileCfg {
+    static constexpr int TZ = 1 << LZ;
+    static constexpr int TT = LZ == 2 ? 160 : 320;
+    static constexpr int MINB = LZ == 2 ? 6 : 3;
+    static constexpr int CAP = LZ == 2 ? 640 : 1088;
+    static constexpr int LCAP = LZ == 2 ? 5120 : 10240;
+    static constexpr size_t DYN = (size_t)CAP * 2 * sizeof(float4) + (size_t)LCAP * 2;
+};
 
-template <int MODE>
-__global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
-    constexpr int HX = 6, NB = HX + 1, NROW = HX * HX, NVOX = 64;
+template <int MODE, int LZ>
+__global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_tile(const StepArgs a) {
+    using C = TileCfg<LZ>;
+    constexpr int kTT = C::TT, kTCap = C::CAP, kTListCap = C::LCAP, TZ = C::TZ;
+    constexpr int HX = 6, HZ = TZ + 2, NB = HX + 1, NROW = HX * HZ, NVOX = 16 * TZ;
+    static_assert(NROW <= 64 && 64 + NVOX <= kTT, "thread roles of the set-up phase");
     extern __shared__ __align__(128) unsigned char dsm[];
     float4* srec = reinterpret_cast<float4*>(dsm);        // staged force records (two float4 each)
     uint16_t* clist = reinterpret_cast<uint16_t*>(srec + 2 * kTCap);   // per-voxel candidate lists
@@ -485,7 +496,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
     __shared__ uint32_t s_vox_loff[NVOX + 1];   // list offset of each core voxel
     __shared__ uint32_t s_vox_toff[NVOX + 1];   // first target number of each core voxel
     __shared__ uint16_t s_vp_off[NVOX][9];      // offset of each neighbour row inside a voxel's list
-    __shared__ uint8_t s_tvox[kTCap];           // core voxel of each target
+    __shared__ uint8_t s_tvox[kTCap];           // core voxel of each target (< 128)
     __shared__ int s_flag;                       // copy timeout
     __shared__ __align__(8) uint64_t s_bar;
 
@@ -510,7 +521,7 @@ __global__ void __launch_bounds__(kTT, 6) k_force_tile(const StepArgs a) {
         const uint32_t rest = lt / (uint32_t)g.nt[0];
         const int by = (int)(rest % (uint32_t)g.nt[1]);
         const int bz = (int)(rest / (uint32_t)g.nt[1]);
-        const int x_lo = 4 * bx - 1, y_lo = 4 * by - 1, z_lo = 4 * bz - 1;
+        const int x_lo = 4 * bx - 1, y_lo = 4 * by - 1, z_lo = TZ * bz - 1;
         // 1. halo row table: row rr = (y - y_lo) + 6 (z - z_lo); boundary k of a
         // row is the start of its voxel x_lo + k (k = 6: the end of the row)
         for (int w = tid; w < NROW * NB; w += kTT) {
@@ -826,23 +837,34 @@ __global__ void __launch_bounds__(kCellBlock) k_pair_stats(const StepArgs a, con
 }
 
 // ---- tile kernel launch ----
-template <int MODE>
+template <int MODE, int LZ>
 cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
     static bool configured = false;
-    auto k = k_force_tile<MODE>;
+    auto k = k_force_tile<MODE, LZ>;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileDynSmem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg<LZ>::DYN);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k<<<grid, kTT, kTileDynSmem, s>>>(a);
+    k<<<grid, TileCfg<LZ>::TT, TileCfg<LZ>::DYN, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int LZ>
+int tile_grid_for(int sms) {
+    int nb = 0;
+    cudaFuncSetAttribute(k_force_tile<kMixedKahan, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)TileCfg<LZ>::DYN);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_tile<kMixedKahan, LZ>, TileCfg<LZ>::TT,
+                                                  TileCfg<LZ>::DYN);
+    return sms * (nb > 0 ? nb : 1);
 }
 
 }  // namespace
 
 bool tile_shape_supported(int ltx, int lty, int ltz) {
-    return ltx == 2 && lty == 2 && ltz == 2;
+    return ltx == 2 && lty == 2 && (ltz == 2 || ltz == 3);
 }
 
 int force_max_blocks_per_sm(int mode, int block) {
@@ -857,10 +879,7 @@ int force_max_blocks_per_sm(int mode, int block) {
 }
 
 int tile_kernel_grid(const StepArgs& a, int sms) {
-    (void)a;
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_tile<kMixedKahan>, kTT, kTileDynSmem);
-    return sms * (nb > 0 ? nb : 1);
+    return a.ltz == 3 ? tile_grid_for<3>(sms) : tile_grid_for<2>(sms);
 }
 
 cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
@@ -873,8 +892,12 @@ cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
 
 cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
-    if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos>(a, grid, s);
-    return launch_tile_mode<kMixedKahan>(a, grid, s);
+    if (a.ltz == 3) {
+        if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos, 3>(a, grid, s);
+        return launch_tile_mode<kMixedKahan, 3>(a, grid, s);
+    }
+    if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos, 2>(a, grid, s);
+    return launch_tile_mode<kMixedKahan, 2>(a, grid, s);
 }
 
 cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s) {

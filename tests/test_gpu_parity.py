@@ -230,8 +230,8 @@ def test_nonfinite_state_raises_device_flag():
 
 
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
-@pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1)],
-                         ids=["cells_only", "t444", "t444_all_dense"])
+@pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1), ((4, 4, 8), 32), ((4, 4, 8), 1)],
+                         ids=["cells_only", "t444", "t444_all_dense", "t448", "t448_all_dense"])
 def test_tiled_force_matches_oracle(mode, tiling):
     """The shared-memory tile kernel (dense tiles) and the thread-per-cell
     kernel (the rest) give the same velocities as the oracle, for every tile
@@ -248,15 +248,16 @@ def test_tiled_force_matches_oracle(mode, tiling):
         check_bins(m, pop, mode)
 
 
+@pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8)])
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
-def test_tile_halo_overflow_falls_back(mode):
+def test_tile_halo_overflow_falls_back(mode, tile):
     """A crowd whose tile halo exceeds the shared-memory capacity is handed
     back to the thread-per-cell kernel."""
     rng = np.random.Generator(np.random.PCG64(31))
-    xyz = rng.uniform(0.0, 55.0, size=(3000, 3))
-    pop = H.tiny_population(xyz, [0] * 3, [240] * 3)
+    xyz = rng.uniform(250.0, 305.0, size=(3000, 3))  # inside an interior tile of either shape
+    pop = H.tiny_population(xyz, [0] * 3, [720] * 3)
     with H.make(pop, mode) as m:
-        m.set_tiling((4, 4, 4), 32)
+        m.set_tiling(tile, 32)
         v = m.compute_velocities()
     vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
     assert H.rel_err(v, vref) <= H.TOL_V_MIXED
