@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // Step 1c: every cell goes to start[key] + slot, carrying (id, A index).  The
 // slot is taken by counting the voxel's histogram entry back down, which
 // leaves the histogram zero for its reuse as the next step's accumulator; the
-// slot order inside a voxel comes from the atomics and k_canon makes it
+// slot order inside a voxel comes from the atomics and k_canon_rank makes it
 // canonical.
 __global__ void k_scatter(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -167,14 +167,10 @@ __global__ void k_scatter(const StepArgs a) {
 }
 
 // Step 1d: rank each cell inside its voxel by caller index (ids are unique),
-// giving its final voxel-order position f; record perm[f], the key, the id,
-// the force record of the cell (position relative to the grid centre as hi on
-// the q grid + 16-bit residual, radius, coefficient square roots) and, in the
-// mixed modes, its state (position, compensation, previous velocity) in B
-// order for the force kernels.
-__global__ void k_canon(const StepArgs a) {
+// giving its final voxel-order position f; record perm[f] (its A index), its
+// key and its id.
+__global__ void k_canon_rank(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    const size_t np = a.npad;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const unsigned long long e = a.tmp[q];
         const uint32_t id = (uint32_t)(e >> 32);
@@ -195,6 +191,24 @@ __global__ void k_canon(const StepArgs a) {
         a.perm[f] = src;
         a.vkey_s[f] = k;
         a.B.id[f] = id;  // written here, so the next state's slot map is complete even if a force kernel aborts
+    }
+}
+
+// Step 1e: in voxel order f, gather each cell from its A position and write its
+// force record (position relative to the grid centre as hi on the q grid +
+// 16-bit residual, radius, coefficient square roots) and, in the mixed modes,
+// its state (position, compensation, previous velocity) for the force kernels.
+// Cells that stay in their voxel keep their relative order, so both the reads
+// at perm[f] and the writes at f are close to sequential.
+__global__ void k_canon_gather(const StepArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < a.n; f += stride) {
+        const uint32_t src = a.perm[f];
+        if (src >= a.n) {  // only after an earlier device error
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
         const int r = rep_of_cell(a.grids, a.nrep, f);
         const GridDev& g = a.grids[r];
         float hi[3], lo[3];
@@ -353,7 +367,8 @@ cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    k_canon<<<grid, 256, 0, s>>>(a);
+    k_canon_rank<<<grid, 256, 0, s>>>(a);
+    k_canon_gather<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
