@@ -86,6 +86,22 @@ def parse():
     return p.parse_args()
 
 
+def reduce_max(x: float, pg, device) -> float:
+    """Largest x over the ranks (the slowest rank sets the job's time); x
+    itself without a process group."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job cell-steps/s: every rank advances its own replica by `steps`."""
+    return cells_per_rank * world * steps / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -417,14 +433,11 @@ def main():
     phases, psteps = m.read_profile() if profile else ({}, 0)
     if profile:
         m.set_profiling(False)
-    t_max = ms
+    t_max = reduce_max(ms, pg, "cuda")
     if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
         pg.barrier()
     total_cells = n * ws
-    value = total_cells * args.steps / (t_max * 1e-3)
+    value = job_throughput(n, ws, args.steps, t_max * 1e-3)
     if not profile:  # graph run: phases from a short profiled pass after the timed region
         m.set_profiling(True)
         m.step(max(2, min(20, args.steps)))
@@ -453,12 +466,8 @@ def main():
             m.write_positions(xh)
             m.step(1)
             m.positions(out=xh)
-        te = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([te], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": total_cells * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
+        te = reduce_max(time.perf_counter() - t0, pg, "cuda")
+        e2e = {"value": job_throughput(n, ws, args.e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": 24 * n,
                "d2h_bytes_per_step": 24 * n, "steps": args.e2e_steps,
                "path": "mech_write_positions (pinned host) -> mech_step(1) -> mech_read_positions (pinned host)"}
     stats = m.pair_stats() if profile else None  # (candidates, interacting pairs) of the final positions
