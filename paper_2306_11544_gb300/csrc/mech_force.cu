@@ -303,15 +303,23 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
     const float4 li = record_lo(pi, qi, g.qs);
     const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
     acc.zero();
-#pragma unroll 1
-    for (int p = 0; p < 9; ++p) {
-        const uint32_t rb = (occ9 >> (3 * p)) & 7u;
-        if (!rb) continue;
+    // One iteration per run of occupied voxels in a row, lowest bit first: rows
+    // (dz, dy) in lexicographic order, voxels along x inside a row (the
+    // candidate order).  A run's cells are one contiguous range of the sorted
+    // records, so it needs two start[] entries.  A warp's sequential steps are
+    // then its lanes' largest run count, not the union of their occupied voxels.
+    uint32_t bits = occ9;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        const int p = b / 3, o = b - 3 * p;
+        const uint32_t run = (bits >> b) & (7u >> o);   // this row's remaining bits from o
+        const int len = __ffs(~run) - 1;                // consecutive occupied voxels (1..3)
+        bits &= ~(((1u << len) - 1u) << b);
         const int jz = c.iz + p / 3 - 1, jy = c.iy + p % 3 - 1;
-        const uint32_t row = g.vbase + (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
-        for (int jx = jx0; jx <= jx1; ++jx) {
-            if (!((rb >> (jx - jx0)) & 1u)) continue;
-            const uint32_t s = a.start[row + jx], e = a.start[row + jx + 1];
+        const uint32_t v0 = g.vbase + (uint32_t)(jx0 + o) +
+                            (uint32_t)g.n[0] * ((uint32_t)jy + (uint32_t)g.n[1] * (uint32_t)jz);
+        {
+            const uint32_t s = a.start[v0], e = a.start[v0 + (uint32_t)len];
             for (uint32_t j = s; j < e; ++j) {
                 const float4 pj = a.B.rec[2 * (size_t)j];
                 const float hx = pi.x - pj.x, hy = pi.y - pj.y, hz = pi.z - pj.z;
