@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--precision-study", action="store_true",
                    help="long-horizon study: batched Kahan and FP64-position runs of the 32-replicate ensemble "
                         "against an FP64 run of its smallest replicate; prints one JSON line")
+    p.add_argument("--oracle-timing", action="store_true",
+                   help="time the FP64 oracle on the host cores (all cores and one core) on bounded samples of "
+                        "configs 1, 2, 3 and 5; prints one JSON line")
     p.add_argument("--plain-loop", action="store_true",
                    help="ensembles: also time the plain single-population path looped over replicates")
     return p.parse_args()
@@ -271,6 +274,47 @@ def cpu_baseline(pop):
             "sample": f"one full oracle step (bin+force+AB2, FP64) of all {n} cells, {t:.1f} s"}
 
 
+def oracle_timing(args):
+    """The FP64 oracle on the host cores, per workload, with every core and with
+    one core: cell-steps/s over a bounded sample (stated per entry)."""
+    import oracle
+    from paper_2306_11544_gb300 import synth
+    oracle.build()
+    o = oracle._load()
+    all_cores = o.num_threads()
+    meta = np.random.Generator(np.random.PCG64(np.random.SeedSequence((0, 1))))
+    counts = np.round(np.exp(meta.uniform(np.log(5e5), np.log(5e6), size=32))).astype(np.int64)
+    r5 = int(np.argmin(counts))
+    n5 = int(counts[r5])
+
+    def rep5(f):
+        return synth._rep_spheroid("ensemble_32_long", 0, r5, max(1, int(round(n5 * f))), 8.4, True, steps=10_000)
+
+    # (name, recipe at a cell fraction, steps with all cores, fraction and steps with one core)
+    cases = [("spheroid_2k", lambda f: synth.spheroid_2k(seed=0, scale=f), 100, 1.0, 100),
+             ("spheroid_1m", lambda f: synth.spheroid_1m(seed=0, scale=f), 3, 1 / 16, 1),
+             ("clustered_20m", lambda f: synth.clustered_20m(seed=0, scale=f), 1, 1 / 64, 1),
+             ("ensemble_32_long smallest replicate", rep5, 5, 1 / 8, 1)]
+    out = {"metric": "FP64 oracle cell-steps/s on the host cores", "unit": UNIT, "cores_all": all_cores,
+           "cases": []}
+    for name, make, steps_all, frac1, steps1 in cases:
+        entry = {"workload": name}
+        for cores, frac, steps in ((all_cores, 1.0, steps_all), (1, frac1, steps1)):
+            p = make(frac)
+            o.set_threads(cores)
+            dims = oracle.grid_dims(p.lo, p.hi, p.h)
+            t0 = time.perf_counter()
+            oracle.run(p.xyz, p.R, p.ccr, p.cca, p.A, p.lo, p.h, dims, p.dt, steps)
+            t = time.perf_counter() - t0
+            entry[f"cores_{cores}"] = {"value": p.n * steps / t,
+                                       "sample": f"{p.n} cells (recipe at {frac:g} of the cells) x {steps} steps, "
+                                                 f"{t:.1f} s"}
+        out["cases"].append(entry)
+    o.set_threads(all_cores)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def time_plain_loop(ens, args, stream, torch):
     """The plain single-population API looped over the replicates: one handle
     per replicate, each advanced `steps` steps on the same stream."""
@@ -358,6 +402,8 @@ def main():
         return run_reference(args)
     if args.precision_study:
         return precision_study(args)
+    if args.oracle_timing:
+        return oracle_timing(args)
     ws, rank, local = dist_env()
     import torch
     from paper_2306_11544_gb300 import build as libbuild

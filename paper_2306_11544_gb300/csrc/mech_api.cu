@@ -193,6 +193,7 @@ struct mech {
         a.ccr64 = d_ccr64;
         a.cca64 = d_cca64;
         a.A_f = (float)A;
+        a.A2m1_f = (float)(A * A - 1.0);
         a.dt_f = (float)dt;
         a.A_d = A;
         a.dt_d = dt;

@@ -146,10 +146,12 @@ struct Acc3 {
 //   1 - d/S is formed as (S^2 - d^2) / (S (S + d)), with d^2 and S^2 carried
 //   as unevaluated sums (error-free products and sums), so the cancellation of
 //   1 - d/S near contact costs no accuracy: t and t_a are accurate to a few
-//   ulp even where d/S is close to 1, which a direct 1 - d/S is not.
+//   ulp even where d/S is close to 1, which a direct 1 - d/S is not.  The
+//   adhesion term uses (A S)^2 - d^2 = S^2 (A^2 - 1) + (S^2 - d^2), A2m1 being
+//   A^2 - 1 rounded once.
 __device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
                                           float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
-                                          float A, Acc3& acc) {
+                                          float A, float A2m1, Acc3& acc) {
     const float rx = hx + lx, ry = hy + ly, rz = hz + lz;
     const float d2 = rx * rx + ry * ry + rz * rz;
     float Se;
@@ -166,16 +168,15 @@ __device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx
                          (lx * (2.f * hx + lx) + ly * (2.f * hy + ly) + lz * (2.f * hz + lz));
         const float rd = rsqrtf(d2);
         const float d = d2 * rd;
-        // (A S)^2 - d^2, with A S = AS + eAS
-        const float eAS = fmaf(A, S, -AS) + A * Se;
-        const float A2 = AS * AS;
-        const float gA = (A2 - D) + ((fmaf(AS, AS, -A2) + 2.f * AS * eAS) - De);
+        // g = S^2 - d^2, with S^2 = S2 + eS; then (A S)^2 - d^2 = S^2 (A^2 - 1) + g
+        const float S2 = S * S;
+        const float eS = fmaf(S, S, -S2) + 2.f * S * Se;
+        const float g = (S2 - D) + (eS - De);
+        const float gA = fmaf(S2, A2m1, fmaf(eS, A2m1, g));
         const float ta = __fdividef(gA, AS * (AS + d));
         float cf = -(sccai * sccaj) * (ta * ta);
         if (d < S) {
-            const float S2 = S * S;
-            const float gS = (S2 - D) + ((fmaf(S, S, -S2) + 2.f * S * Se) - De);
-            const float t = __fdividef(gS, S * (S + d));
+            const float t = __fdividef(g, S * (S + d));
             cf += (sccri * sccrj) * (t * t);
         }
         const float sc = cf * rd;
@@ -327,7 +328,7 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
                     const float4 qj = a.B.rec[2 * (size_t)j + 1];
                     const float4 lj = record_lo(pj, qj, g.qs);
                     pair_term(hx, hy, hz, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w, li.w + lj.w, qi.x, qi.y,
-                              qj.x, qj.y, A, acc);
+                              qj.x, qj.y, A, a.A2m1_f, acc);
                 }
             }
         }
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
                         const float4 q2 = srec[2 * jj + 1];
                         const float4 l2 = record_lo(p2, q2, g.qs);
                         pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y, li.z - l2.z, pi.w,
-                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, A, acc);
+                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, A, a.A2m1_f, acc);
                     }
                 }
                 int nix, niy, niz;

@@ -154,6 +154,7 @@ struct StepArgs {
     const double* ccr64;
     const double* cca64;
     float A_f, dt_f;
+    float A2m1_f;          // A^2 - 1 (rounded once)
     double A_d, dt_d;
     int integrate;         // 1: AB2 update; 0: velocities only (positions kept)
     float* vout_f;         // velocities-only output, B order (mixed modes)
