@@ -545,7 +545,10 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (ce == cudaSuccess) ce = launch_load_vprev(a, h->st[0], nullptr, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return bail(fail(MECH_E_CUDA, std::string("initial load: ") + cudaGetErrorString(ce)));
-    h->elem_grid = h->sms * 8;
+    // element-wise kernels (binning): about four cells per thread, so that many
+    // gathers are in flight (measured better than a grid-stride loop over a
+    // few CTAs per SM)
+    h->elem_grid = (int)std::min<int64_t>(std::max<int64_t>(h->sms * 8, (n + 1023) / 1024), 1 << 20);
     h->force_grid = h->sms * force_max_blocks_per_sm(h->mode, h->force_block);
     h->tile_grid = tile_kernel_grid(h->args(0, 1), h->sms);
     *out = h;
