@@ -36,14 +36,16 @@ METRIC = "mechanics cell-steps/s (bin+force+AB2), batched vs plain, at <=1e-3 um
 UNIT = "cell-steps/s"
 # Algorithmic bytes (compulsory HBM traffic) of the fixed byte model.
 FORCE_BYTES_PER_CELL = 84      # read x 24 + params 12 + v_prev 12, write x 24 + v 12
-# Algorithmic FP32 operations of the force phase (definition of the method,
-# counted per operation; a fused multiply-add is two): a neighbour test
-# (difference 3, squares and sum 5, compare 1), an interacting ordered pair
-# (sqrt 1; S, A S, d/(A S), 1 - . 4; square and coefficient 4; d/S and 1 - . 2,
-# square and coefficient 4; c_r - c_a 1; /d 1; times r 3; accumulate 3) and the
-# AB2 update of a cell (5 per component).
-OPS_PER_CANDIDATE = 9
-OPS_PER_ORDERED_PAIR = 23
+# Algorithmic FP32 operations of the force phase, by the method's definition:
+# every cell tests the cells of the 27 voxels around its voxel on the
+# workload's mechanics grid (8 operations: 3 differences, 3 multiply-adds, a
+# compare), each interacting ordered pair adds 30 (square root, reciprocals,
+# the two squared terms, scaling and accumulation), and the AB2 update of a
+# cell 15 (5 per component).  The internal grid the step uses is finer, so the
+# step performs fewer tests than the method's count; the count is the
+# method's, measured on the workload's grid after the timed region.
+OPS_PER_CANDIDATE = 8
+OPS_PER_ORDERED_PAIR = 30
 OPS_PER_CELL_AB2 = 15
 # FP32 peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 ops
 # (fused multiply-add) x 2.07 GHz maximum SM clock.
@@ -516,7 +518,18 @@ def main():
         e2e = {"value": job_throughput(n, ws, args.e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": 24 * n,
                "d2h_bytes_per_step": 24 * n, "steps": args.e2e_steps,
                "path": "mech_write_positions (pinned host) -> mech_step(1) -> mech_read_positions (pinned host)"}
-    stats = m.pair_stats() if profile else None  # (candidates, interacting pairs) of the final positions
+    stats = None
+    if profile:
+        # (neighbour tests, interacting pairs) of the final positions: on the
+        # internal grid the step uses, then on the workload's own voxel grid
+        tests_done, pairs = m.pair_stats()
+        if args.voxel not in ("user", "0"):
+            m.set_internal_voxel(0.0)
+            tests_method, pairs_method = m.pair_stats()
+            assert pairs_method == pairs  # the pair set does not depend on the grid
+        else:
+            tests_method = tests_done
+        stats = (tests_method, tests_done, pairs)
     m.close()
 
     if rank != 0:
@@ -531,7 +544,7 @@ def main():
         # bound is instruction issue, so the roofline is the FP32 one, with the
         # method's operation count from the neighbour statistics of the run
         t_force = (phases["classify"] + phases["tiles"] + phases["cells"]) / psteps * 1e-3
-        cand, pairs = stats
+        cand, cand_done, pairs = stats
         ops = OPS_PER_CANDIDATE * cand + OPS_PER_ORDERED_PAIR * 2 * pairs + OPS_PER_CELL_AB2 * n
         ach = ops / t_force / 1e12
         tr = force_traffic()
@@ -544,9 +557,10 @@ def main():
                 "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
                 "peak_kind": alu_kind,
                 "ops_per_launch": ops,
-                "ops_model": f"{OPS_PER_CANDIDATE}/neighbour test x {cand} + {OPS_PER_ORDERED_PAIR}/ordered pair x "
-                             f"{2 * pairs} + {OPS_PER_CELL_AB2}/cell AB2 x {n}",
-                "candidates": cand, "interacting_pairs": pairs,
+                "ops_model": f"{OPS_PER_CANDIDATE}/neighbour test x {cand} (27 voxels of the workload's grid) + "
+                             f"{OPS_PER_ORDERED_PAIR}/ordered pair x {2 * pairs} + {OPS_PER_CELL_AB2}/cell AB2 x {n}",
+                "neighbour_tests_method": cand, "neighbour_tests_performed": cand_done,
+                "interacting_pairs": pairs,
                 "launch_ms": 1e3 * t_force,
                 "traffic": None if tr is None else tr.get("dram_bytes_per_cell", 0) * n,
                 "traffic_source": None if tr is None else tr.get("source"),
