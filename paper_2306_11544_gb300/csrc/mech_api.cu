@@ -661,7 +661,7 @@ int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t tile_z, i
         auto lg = [](int32_t v) { return v == 4 ? 2 : (v == 8 ? 3 : -1); };
         const int lx = lg(tile_x), ly = lg(tile_y), lz = lg(tile_z);
         if (!tile_shape_supported(lx, ly, lz))
-            return fail(MECH_E_ARG, "supported tiles: 4x4x4 or 4x4x8 voxels (or 0,0,0 to disable)");
+            return fail(MECH_E_ARG, "supported tiles: 4x4x4, 4x4x8 or 8x4x4 voxels (or 0,0,0 to disable)");
         if (dense_min < 1) return fail(MECH_E_ARG, "dense_min must be >= 1");
         h->use_tiles = true;
         if (lx != h->ltx || ly != h->lty || lz != h->ltz) {

@@ -374,11 +374,12 @@ __global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
 
 // A tile is processed by the tile kernel only when its whole halo lies inside
 // the grid (1 <= b and T b + T <= n - 1 on every axis, T the tile's extent):
-// the kernel's shape is then fixed (6 x (TZ + 2) halo rows of 6 voxels around
-// 4 x 4 x TZ core voxels) and its index arithmetic compiles to constants.
+// the kernel's shape is then fixed (6 x (TZ + 2) halo rows of TX + 2 voxels
+// around TX x 4 x TZ core voxels) and its index arithmetic compiles to
+// constants.
 // Tiles at the grid faces go to the thread-per-cell kernel.
-__device__ __forceinline__ bool tile_interior(const GridDev& g, int bx, int by, int bz, int tz) {
-    return bx >= 1 && by >= 1 && bz >= 1 && 4 * bx + 4 <= g.n[0] - 1 && 4 * by + 4 <= g.n[1] - 1 &&
+__device__ __forceinline__ bool tile_interior(const GridDev& g, int bx, int by, int bz, int tx, int tz) {
+    return bx >= 1 && by >= 1 && bz >= 1 && tx * bx + tx <= g.n[0] - 1 && 4 * by + 4 <= g.n[1] - 1 &&
            tz * bz + tz <= g.n[2] - 1;
 }
 
@@ -402,7 +403,7 @@ __global__ void k_tile_classify(const StepArgs a) {
                 const uint32_t lt = t - g.tbase;
                 const uint32_t rest = lt / (uint32_t)g.nt[0];
                 dense = tile_interior(g, (int)(lt % (uint32_t)g.nt[0]), (int)(rest % (uint32_t)g.nt[1]),
-                                      (int)(rest / (uint32_t)g.nt[1]), 1 << a.ltz);
+                                      (int)(rest / (uint32_t)g.nt[1]), 1 << a.ltx, 1 << a.ltz);
             }
             a.tdense[t] = dense ? 1 : 0;
             a.tcount_nxt[t] = 0u;
@@ -477,24 +478,26 @@ __device__ __forceinline__ uint32_t warp_scan_inplace(uint32_t* v, int n) {
     return carry;
 }
 
-// Tile of 4 x 4 x TZ voxels (TZ = 2^LZ, 4 or 8): threads per CTA (about one
-// per target), CTAs per SM, staged halo records (a dense core 4x4x4 tile holds
-// ~490 of 216 halo voxels) and candidate-list entries per tile.
-template <int LZ>
+// Tile of TX x 4 x TZ voxels (TX = 2^LX, TZ = 2^LZ; 4x4x4, 4x4x8 or 8x4x4):
+// threads per CTA (about one per target), CTAs per SM, staged halo records (a
+// dense core 4x4x4 tile holds ~490 of its 216 halo voxels) and candidate-list
+// entries per tile.
+template <int LX, int LZ>
 struct TileCfg {
-    static constexpr int TZ = 1 << LZ;
-    static constexpr int TT = LZ == 2 ? 160 : 320;
-    static constexpr int MINB = LZ == 2 ? 6 : 3;
-    static constexpr int CAP = LZ == 2 ? 640 : 1088;
-    static constexpr int LCAP = LZ == 2 ? 5120 : 10240;
+    static constexpr int TX = 1 << LX, TZ = 1 << LZ, NV = 4 * TX * TZ;
+    static constexpr int TT = NV <= 64 ? 160 : 320;
+    static constexpr int MINB = NV <= 64 ? 6 : 3;
+    static constexpr int CAP = NV <= 64 ? 640 : 1088;
+    static constexpr int LCAP = NV <= 64 ? 5120 : 10240;
     static constexpr size_t DYN = (size_t)CAP * 2 * sizeof(float4) + (size_t)LCAP * 2;
 };
 
-template <int MODE, int LZ>
-__global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_tile(const StepArgs a) {
-    using C = TileCfg<LZ>;
-    constexpr int kTT = C::TT, kTCap = C::CAP, kTListCap = C::LCAP, TZ = C::TZ;
-    constexpr int HX = 6, HZ = TZ + 2, NB = HX + 1, NROW = HX * HZ, NVOX = 16 * TZ;
+template <int MODE, int LX, int LZ>
+__global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_force_tile(const StepArgs a) {
+    using C = TileCfg<LX, LZ>;
+    constexpr int kTT = C::TT, kTCap = C::CAP, kTListCap = C::LCAP, TX = C::TX, TZ = C::TZ;
+    // halo rows run along x: RL voxels each, HY x HZ of them
+    constexpr int RL = TX + 2, HY = 6, HZ = TZ + 2, NB = RL + 1, NROW = HY * HZ, NVOX = C::NV;
     static_assert(NROW <= 64 && 64 + NVOX <= kTT, "thread roles of the set-up phase");
     extern __shared__ __align__(128) unsigned char dsm[];
     float4* srec = reinterpret_cast<float4*>(dsm);        // staged force records (two float4 each)
@@ -530,12 +533,12 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
         const uint32_t rest = lt / (uint32_t)g.nt[0];
         const int by = (int)(rest % (uint32_t)g.nt[1]);
         const int bz = (int)(rest / (uint32_t)g.nt[1]);
-        const int x_lo = 4 * bx - 1, y_lo = 4 * by - 1, z_lo = TZ * bz - 1;
+        const int x_lo = TX * bx - 1, y_lo = 4 * by - 1, z_lo = TZ * bz - 1;
         // 1. halo row table: row rr = (y - y_lo) + 6 (z - z_lo); boundary k of a
-        // row is the start of its voxel x_lo + k (k = 6: the end of the row)
+        // row is the start of its voxel x_lo + k (k = RL: the end of the row)
         for (int w = tid; w < NROW * NB; w += kTT) {
             const int rr = w / NB, k = w - rr * NB;
-            const int yy = y_lo + rr % HX, zz = z_lo + rr / HX;
+            const int yy = y_lo + rr % HY, zz = z_lo + rr / HY;
             const uint32_t rowv = g.vbase + (uint32_t)g.n[0] * ((uint32_t)yy + (uint32_t)g.n[1] * (uint32_t)zz);
             s_row_vb[rr][k] = a.start[rowv + (uint32_t)(x_lo + k)];
         }
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
             for (int rr = (int)lane; rr < NROW; rr += 32) {
                 const uint32_t gs = s_row_vb[rr][0];
                 s_row_gs[rr] = gs;
-                s_row_off[rr] = s_row_vb[rr][HX] - gs;  // row length, scanned below
+                s_row_off[rr] = s_row_vb[rr][RL] - gs;  // row length, scanned below
             }
             __syncwarp();
             const uint32_t total = warp_scan_inplace(s_row_off, NROW);
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
         // expects the bytes of all rows (its single arrival comes with them)
         if (tid < NROW) {
             const int rr = tid;
-            const uint32_t len = s_row_vb[rr][HX];
+            const uint32_t len = s_row_vb[rr][RL];
             fence_proxy_async();
             if (tid == 0)
                 mbar_arrive_expect_tx(&s_bar, total * 2u * (uint32_t)sizeof(float4) +
@@ -576,18 +579,18 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
         } else if (tid >= 64 && tid < 64 + NVOX) {
             // 3a (overlaps the copies). per-voxel list lengths, neighbour-row offsets, target counts
             const int v = tid - 64;
-            const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
+            const int cx = v & (TX - 1), cy = (v >> LX) & 3, cz = v >> (LX + 2);
             uint32_t len = 0;
             int p = 0;
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy, ++p) {
-                    const int r2 = (cy + dy) + HX * (cz + dz);
+                    const int r2 = (cy + dy) + HY * (cz + dz);
                     s_vp_off[v][p] = (uint16_t)len;
                     len += s_row_vb[r2][cx + 3] - s_row_vb[r2][cx];
                 }
-            const int rr = (cy + 1) + HX * (cz + 1);
+            const int rr = (cy + 1) + HY * (cz + 1);
             s_vox_loff[v] = len;
             s_vox_toff[v] = s_row_vb[rr][cx + 2] - s_row_vb[rr][cx + 1];
         }
@@ -618,8 +621,8 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
         // and the core voxel of every target
         for (int w = tid; w < NVOX * 9; w += kTT) {
             const int v = w / 9, p = w - v * 9;
-            const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
-            const int r2 = (cy + p % 3) + HX * (cz + p / 3);
+            const int cx = v & (TX - 1), cy = (v >> LX) & 3, cz = v >> (LX + 2);
+            const int r2 = (cy + p % 3) + HY * (cz + p / 3);
             uint32_t o = s_vox_loff[v] + s_vp_off[v][p];
             const uint32_t j1 = s_row_off[r2] + s_row_vb[r2][cx + 3];
             for (uint32_t j = s_row_off[r2] + s_row_vb[r2][cx]; j < j1; ++j) clist[o++] = (uint16_t)j;
@@ -636,8 +639,8 @@ __global__ void __launch_bounds__(TileCfg<LZ>::TT, TileCfg<LZ>::MINB) k_force_ti
             if (valid) {
                 const int v = s_tvox[t];
                 const uint32_t k = t - s_vox_toff[v];
-                const int cx = v & 3, cy = (v >> 2) & 3, cz = v >> 4;
-                const int rr = (cy + 1) + HX * (cz + 1);
+                const int cx = v & (TX - 1), cy = (v >> LX) & 3, cz = v >> (LX + 2);
+                const int rr = (cy + 1) + HY * (cz + 1);
                 const uint32_t in_row = s_row_vb[rr][cx + 1] + k;
                 q = s_row_gs[rr] + in_row;
                 const uint32_t si = s_row_off[rr] + in_row;
@@ -846,34 +849,41 @@ __global__ void __launch_bounds__(kCellBlock) k_pair_stats(const StepArgs a, con
 }
 
 // ---- tile kernel launch ----
-template <int MODE, int LZ>
+template <int MODE, int LX, int LZ>
 cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
+    using C = TileCfg<LX, LZ>;
     static bool configured = false;
-    auto k = k_force_tile<MODE, LZ>;
+    auto k = k_force_tile<MODE, LX, LZ>;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg<LZ>::DYN);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::DYN);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k<<<grid, TileCfg<LZ>::TT, TileCfg<LZ>::DYN, s>>>(a);
+    k<<<grid, C::TT, C::DYN, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int LZ>
+template <int LX, int LZ>
 int tile_grid_for(int sms) {
+    using C = TileCfg<LX, LZ>;
     int nb = 0;
-    cudaFuncSetAttribute(k_force_tile<kMixedKahan, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)TileCfg<LZ>::DYN);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_tile<kMixedKahan, LZ>, TileCfg<LZ>::TT,
-                                                  TileCfg<LZ>::DYN);
+    cudaFuncSetAttribute(k_force_tile<kMixedKahan, LX, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)C::DYN);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_tile<kMixedKahan, LX, LZ>, C::TT, C::DYN);
     return sms * (nb > 0 ? nb : 1);
+}
+
+template <int MODE>
+cudaError_t launch_tile_shape(const StepArgs& a, int grid, cudaStream_t s) {
+    if (a.ltx == 3) return launch_tile_mode<MODE, 3, 2>(a, grid, s);
+    if (a.ltz == 3) return launch_tile_mode<MODE, 2, 3>(a, grid, s);
+    return launch_tile_mode<MODE, 2, 2>(a, grid, s);
 }
 
 }  // namespace
 
 bool tile_shape_supported(int ltx, int lty, int ltz) {
-    return ltx == 2 && lty == 2 && (ltz == 2 || ltz == 3);
+    return lty == 2 && ((ltx == 2 && (ltz == 2 || ltz == 3)) || (ltx == 3 && ltz == 2));
 }
 
 int force_max_blocks_per_sm(int mode, int block) {
@@ -888,7 +898,8 @@ int force_max_blocks_per_sm(int mode, int block) {
 }
 
 int tile_kernel_grid(const StepArgs& a, int sms) {
-    return a.ltz == 3 ? tile_grid_for<3>(sms) : tile_grid_for<2>(sms);
+    if (a.ltx == 3) return tile_grid_for<3, 2>(sms);
+    return a.ltz == 3 ? tile_grid_for<2, 3>(sms) : tile_grid_for<2, 2>(sms);
 }
 
 cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
@@ -901,12 +912,8 @@ cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
 
 cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
-    if (a.ltz == 3) {
-        if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos, 3>(a, grid, s);
-        return launch_tile_mode<kMixedKahan, 3>(a, grid, s);
-    }
-    if (a.mode == kMixedFP64Pos) return launch_tile_mode<kMixedFP64Pos, 2>(a, grid, s);
-    return launch_tile_mode<kMixedKahan, 2>(a, grid, s);
+    if (a.mode == kMixedFP64Pos) return launch_tile_shape<kMixedFP64Pos>(a, grid, s);
+    return launch_tile_shape<kMixedKahan>(a, grid, s);
 }
 
 cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s) {

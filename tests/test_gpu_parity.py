@@ -230,8 +230,10 @@ def test_nonfinite_state_raises_device_flag():
 
 
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
-@pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1), ((4, 4, 8), 32), ((4, 4, 8), 1)],
-                         ids=["cells_only", "t444", "t444_all_dense", "t448", "t448_all_dense"])
+@pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1), ((4, 4, 8), 32), ((4, 4, 8), 1),
+                                    ((8, 4, 4), 32), ((8, 4, 4), 1)],
+                         ids=["cells_only", "t444", "t444_all_dense", "t448", "t448_all_dense", "t844",
+                              "t844_all_dense"])
 def test_tiled_force_matches_oracle(mode, tiling):
     """The shared-memory tile kernel (dense tiles) and the thread-per-cell
     kernel (the rest) give the same velocities as the oracle, for every tile
@@ -248,7 +250,7 @@ def test_tiled_force_matches_oracle(mode, tiling):
         check_bins(m, pop, mode)
 
 
-@pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8)])
+@pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
 def test_tile_halo_overflow_falls_back(mode, tile):
     """A crowd whose tile halo exceeds the shared-memory capacity is handed
