@@ -30,6 +30,8 @@
 // and records are used as staged, with no per-tile frame shift.  No FP64
 // arithmetic runs in any candidate loop (FP64 is ~1/62 of FP32 throughput on
 // this GPU).
+#include <atomic>
+
 #include "mech_internal.cuh"
 
 namespace mk {
@@ -852,12 +854,18 @@ __global__ void __launch_bounds__(kCellBlock) k_pair_stats(const StepArgs a, con
 template <int MODE, int LX, int LZ>
 cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
     using C = TileCfg<LX, LZ>;
-    static bool configured = false;
+    // the dynamic shared-memory limit is a per-device function attribute: set
+    // it once for each device this process launches on (devices 0..63)
+    static std::atomic<unsigned long long> configured{0ull};
     auto k = k_force_tile<MODE, LX, LZ>;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::DYN);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::DYN);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.fetch_or(bit);
     }
     k<<<grid, C::TT, C::DYN, s>>>(a);
     return cudaGetLastError();
