@@ -373,3 +373,43 @@ def test_pair_stats_match_oracle(name, voxel, mode):
     pref = oracle.pairs(x, pop.R, pop.A, pop.lo, pop.h, H.dims_of(pop))
     assert pairs == pref.shape[0]
     assert pairs > 0 and cand > 2 * pairs
+
+
+@pytest.mark.parametrize("tile", [(4, 4, 8), (8, 4, 4)])
+def test_runs_are_bitwise_reproducible(tile):
+    """The slot order the scatter takes from atomics never reaches the result:
+    two handles advanced the same way end bitwise equal (dense tiles, sparse
+    cells and hand-back paths all active)."""
+    pop = synth.clustered_20m(seed=23, scale=0.002)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    xs = []
+    for _ in range(2):
+        with H.make(pop, "kahan", voxel=hmin) as m:
+            m.set_tiling(tile, 16)
+            m.step(12)
+            xs.append(m.read_state())
+    for k in ("xyz", "vprev", "comp"):
+        assert np.array_equal(xs[0][k], xs[1][k]), k
+
+
+def test_pair_stats_of_a_batch_sum_over_replicates():
+    """Neighbour statistics of a batched handle are the sums of its replicates'
+    statistics, and the pairs are the oracle's pairs replicate by replicate."""
+    from paper_2306_11544_gb300 import mech
+    ens = synth.ensemble_256(seed=24, scale=0.02, n_rep=5)
+    with mech.Mech.from_ensemble(ens, mode="mixed") as b:
+        b.step(2)
+        cand_b, pairs_b = b.pair_stats()
+        xb = b.positions()
+    cand, pairs, pref, off = 0, 0, 0, 0
+    for p in ens.reps:
+        x = xb[off:off + p.n]
+        off += p.n
+        with H.make(p, "mixed") as m:
+            m.load_state({"xyz": x, "vprev": np.zeros_like(x), "step": 0})
+            c, q = m.pair_stats()
+        cand += c
+        pairs += q
+        pref += oracle.pairs(x, p.R, p.A, p.lo, p.h, H.dims_of(p)).shape[0]
+    assert (cand_b, pairs_b) == (cand, pairs)
+    assert pairs_b == pref
