@@ -341,7 +341,7 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
 // Every cell not owned by a dense tile: the cells listed by k_sparse_list, or
 // all cells when tiles are off.
 template <int MODE>
-__global__ void __launch_bounds__(kCellBlock) k_force_cells(const StepArgs a) {
+__global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
