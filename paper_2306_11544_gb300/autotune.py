@@ -51,7 +51,7 @@ def candidates(min_voxel: float, user_voxel: float):
     sides = [s for s in sides if s <= max(up(user_voxel), up(min_voxel))]
     out = []
     for h in sides:
-        for tile, dmin in (((4, 4, 8), 16), ((8, 4, 4), 16), ((4, 4, 4), 16), ((4, 4, 4), 32), (None, 0)):
+        for tile, dmin in (((4, 4, 8), 48), ((4, 4, 8), 96), ((8, 4, 4), 48), ((4, 4, 4), 32), (None, 0)):
             for block in (128, 256):
                 out.append({"voxel": h, "tile": tile, "dense_min": dmin, "block": block})
     return out
