@@ -212,6 +212,36 @@ def test_write_positions_then_step_matches_fresh_handle():
     assert np.array_equal(v, vref)
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "kahan"])
+def test_position_transfers_are_exact(mode, pinned):
+    """1.3M cells, from pageable and from pinned host memory: after steps have
+    reordered the cells into voxel order, the position read matches the state
+    read bit for bit, and a write is read back exactly (Kahan mode: as the
+    FP32 value and compensation it stores)."""
+    import torch
+    pop = synth.clustered_20m(seed=31, scale=0.065)
+    n = pop.n
+    assert 2 * 2**19 < n < 3 * 2**19
+    buf = (torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy() if pinned
+           else np.empty((n, 3)))
+    with H.make(pop, mode) as m:
+        m.set_tiling((4, 4, 8), 48)
+        m.step(3)
+        st = m.read_state()
+        x = m.positions(out=buf).copy()
+        assert np.array_equal(x, st["xyz"] - st["comp"] if mode == "kahan" else st["xyz"])
+        rng = np.random.Generator(np.random.PCG64(32))
+        buf[:] = x + rng.normal(0, 0.3, size=x.shape)
+        w = buf.copy()
+        m.write_positions(buf)
+        back = m.positions()
+    if mode == "kahan":
+        hi = w.astype(np.float32).astype(np.float64)
+        w = hi - (hi - w).astype(np.float32).astype(np.float64)
+    assert np.array_equal(back, w)
+
+
 def test_nonfinite_state_raises_device_flag():
     """A cell pushed to a non-finite position is reported, not hidden (the
     fault is made on the host: positions written with a huge value overflow
@@ -263,6 +293,38 @@ def test_tile_halo_overflow_falls_back(mode, tile):
         v = m.compute_velocities()
     vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
     assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+
+
+@pytest.mark.parametrize("radii", ["uniform", "spread"])
+@pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_tile_scan_keeps_pairs_at_the_cutoff(mode, tile, radii):
+    """Every interacting pair of a jittered cubic lattice (13,824 cells, every
+    tile dense) sits just inside the adhesion cutoff, 1 - d/(A S) between
+    6e-4 and 5.4e-3, and all diagonal pairs are out of range: each velocity is
+    a sum of six of the smallest possible terms, so a pair dropped by the tile
+    kernel's cutoff test anywhere in a tile changes a velocity by its whole
+    size.  "spread": the lattice radius lies between the smallest and the
+    largest radius of the population (two isolated cells), which loosens the
+    test through its R_max and C0 bounds."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    R0 = 7.5 if radii == "spread" else 8.41
+    AS = 1.25 * 2 * R0
+    g = (np.arange(24) - 11.5) * AS * (1 - 3e-3)
+    xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    xyz += rng.uniform(-1.2e-3 * AS, 1.2e-3 * AS, size=xyz.shape)
+    R = np.full(len(xyz), R0)
+    if radii == "spread":
+        xyz = np.vstack([xyz, [[285.0, 285.0, 285.0], [-285.0, 285.0, -285.0]]])
+        R = np.append(R, [6.0, 9.0])
+    pop = H.tiny_population(xyz, [-300] * 3, [300] * 3, R=R)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    with H.make(pop, mode, voxel=hmin) as m:
+        m.set_tiling(tile, 1)
+        v = m.compute_velocities()
+    vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert (np.abs(vref[:13824]).max(axis=1) > 0).all()
+    assert H.rel_err(v, vref) <= 1e-4
 
 
 def test_internal_voxel_with_tiles_over_steps():
