@@ -196,8 +196,9 @@ __global__ void k_canon_rank(const StepArgs a) {
 
 // Step 1e: in voxel order f, gather each cell from its A position and write its
 // force record (position relative to the grid centre as hi on the q grid +
-// 16-bit residual, radius, coefficient square roots) and, in the mixed modes,
-// its state (position, compensation, previous velocity) for the force kernels.
+// 16-bit residual, radius, coefficient square roots).  The rest of the state
+// (position, compensation, previous velocity) stays in A order: the force
+// kernels read it at perm[f] for the AB2 update and write the new state at f.
 // Cells that stay in their voxel keep their relative order, so both the reads
 // at perm[f] and the writes at f are close to sequential.
 __global__ void k_canon_gather(const StepArgs a) {
@@ -223,9 +224,6 @@ __global__ void k_canon_gather(const StepArgs a) {
                 const float sv = two_sum(s1, -__fadd_rn(g.oc_lo[d], c), e2);
                 hi[d] = quantize_hi(sv, g.q, g.inv_q);
                 lo[d] = __fadd_rn(__fsub_rn(sv, hi[d]), __fadd_rn(e1, e2));
-                a.B.posf[d * np + f] = xh;
-                a.B.comp[d * np + f] = c;
-                a.B.vpf[d * np + f] = a.A.vpf[d * np + src];
             }
         } else {
 #pragma unroll
@@ -240,10 +238,6 @@ __global__ void k_canon_gather(const StepArgs a) {
                 } else {
                     hi[d] = __double2float_rn(rr);
                     lo[d] = 0.f;
-                }
-                if (a.mode == kMixedFP64Pos) {
-                    a.B.pos64[d * np + f] = x;
-                    a.B.vpf[d * np + f] = a.A.vpf[d * np + src];
                 }
             }
         }

@@ -192,9 +192,8 @@ __device__ __forceinline__ bool candidate_hit(float hx, float hy, float hz, floa
     return hx * hx + hy * hy + hz * hz < c * c;
 }
 
-// State of cell q (B order) that its AB2 update reads: previous velocity and
-// position (FP64, or FP32 x_hi with its compensation).  Its state was copied
-// into B order by the canonicalisation pass.
+// State that the AB2 update of a cell reads: previous velocity and position
+// (FP64, or FP32 x_hi with its compensation), from the A order.
 template <int MODE>
 struct CellState {
     float vp[3];
@@ -202,25 +201,37 @@ struct CellState {
     double x[3];         // FP64-position mode
 };
 
+// Position in the A (previous) order of the cell at B position q.
+__device__ __forceinline__ uint32_t a_slot(const StepArgs& a, uint32_t q) {
+    uint32_t src = a.perm[q];
+    if (src >= a.n) {  // only after an earlier device error
+        atomicOr(a.err, kErrIndex);
+        src = q;
+    }
+    return src;
+}
+
+// The state is read where the previous step left it (A order, slot src =
+// perm[q]): the canonicalisation moves only the force records into B order.
 template <int MODE>
-__device__ __forceinline__ CellState<MODE> load_cell_state(const StepArgs& a, uint32_t q) {
+__device__ __forceinline__ CellState<MODE> load_cell_state(const StepArgs& a, uint32_t src) {
     const size_t np = a.npad;
     CellState<MODE> st;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        st.vp[d] = a.B.vpf[d * np + q];
+        st.vp[d] = a.A.vpf[d * np + src];
         if (MODE == kMixedFP64Pos) {
-            st.x[d] = a.B.pos64[d * np + q];
+            st.x[d] = a.A.pos64[d * np + src];
         } else {
-            st.xh[d] = a.B.posf[d * np + q];
-            st.cc[d] = a.B.comp[d * np + q];
+            st.xh[d] = a.A.posf[d * np + src];
+            st.cc[d] = a.A.comp[d * np + src];
         }
     }
     return st;
 }
 
-// AB2 update of cell q (B order) in place; returns the next step's voxel key
-// and its voxel coordinates.
+// AB2 update of cell q: state st read from the A order, new state written at q
+// in the B order; returns the next step's voxel key and its voxel coordinates.
 template <int MODE>
 __device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& g, uint32_t q,
                                               const CellState<MODE>& st, float ax, float ay, float az, int& nix,
@@ -232,27 +243,28 @@ __device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& 
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float inc = a.dt_f * (1.5f * v[d] - 0.5f * st.vp[d]);
+        // the whole state is written in B order; a velocities-only pass
+        // (integrate 0) writes it unchanged
         if (MODE == kMixedFP64Pos) {
             const double xn = a.integrate ? __dadd_rn(st.x[d], (double)inc) : st.x[d];
-            if (a.integrate) a.B.pos64[d * np + q] = xn;
+            a.B.pos64[d * np + q] = xn;
             xf[d] = __double2float_rn(xn);
             finite = finite && isfinite(xn);
         } else {
-            float xh = st.xh[d];
+            float xh = st.xh[d], cc = st.cc[d];
             if (a.integrate) {
-                float cc = st.cc[d];
                 const float y = __fsub_rn(inc, cc);
                 const float t = __fadd_rn(xh, y);
                 cc = __fsub_rn(__fsub_rn(t, xh), y);
                 xh = t;
-                a.B.posf[d * np + q] = xh;
-                a.B.comp[d * np + q] = cc;
             }
+            a.B.posf[d * np + q] = xh;
+            a.B.comp[d * np + q] = cc;
             xf[d] = xh;
             finite = finite && isfinite(xh);
         }
-        if (a.integrate) a.B.vpf[d * np + q] = v[d];
-        else a.vout_f[d * np + q] = v[d];
+        a.B.vpf[d * np + q] = a.integrate ? v[d] : st.vp[d];
+        if (!a.integrate) a.vout_f[d * np + q] = v[d];
         finite = finite && isfinite(v[d]);
     }
     if (!finite) atomicOr(a.err, kErrNonFinite);
@@ -263,9 +275,9 @@ __device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& 
 }
 
 template <int MODE>
-__device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, float ax, float ay,
-                                                 float az, int& nix, int& niy, int& niz) {
-    const CellState<MODE> st = load_cell_state<MODE>(a, q);
+__device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, uint32_t src,
+                                                 float ax, float ay, float az, int& nix, int& niy, int& niz) {
+    const CellState<MODE> st = load_cell_state<MODE>(a, src);
     return ab2_apply<MODE>(a, g, q, st, ax, ay, az, nix, niy, niz);
 }
 
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
                 q = idx;
                 key = a.vkey_s[q];
             }
-            const CellState<MODE> st = load_cell_state<MODE>(a, q);  // issued before the walk
+            const CellState<MODE> st = load_cell_state<MODE>(a, a_slot(a, q));  // issued before the walk
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(key, g);
@@ -645,6 +657,7 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                 const int rr = (cy + 1) + HY * (cz + 1);
                 const uint32_t in_row = s_row_vb[rr][cx + 1] + k;
                 q = s_row_gs[rr] + in_row;
+                const uint32_t src = a_slot(a, q);  // its state, read after the scan
                 const uint32_t si = s_row_off[rr] + in_row;
                 const float4 pi = srec[2 * si];
                 const float4 qi = srec[2 * si + 1];
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                     }
                 }
                 int nix, niy, niz;
-                nkey = ab2_epilogue<MODE>(a, g, q, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
+                nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
                 ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
             }
             next_step_counts(a, q, nkey, ntile, valid);

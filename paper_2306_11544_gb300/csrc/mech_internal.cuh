@@ -20,9 +20,11 @@
 //                                 four 16-bit fixed-point residuals: x_lo,
 //                                 y_lo, z_lo in units of q / 2^15 and
 //                                 R - (float)R in units of ulp(R) / 2^15
-//     The canonicalisation pass also copies each cell's state (positions,
-//     compensation, previous velocity) into B order, so the force kernels
-//     read and update their own cells contiguously.
+//     The canonicalisation pass writes only the force records in B order;
+//     the force kernels read each cell's state (positions, compensation,
+//     previous velocity) in A order at perm[q] (nearly sequential: cells that
+//     stay in their voxel keep their relative order) and write its new state
+//     at q in B order.
 //   * binning scratch: key [n] (next voxel of each cell in A order), vkey_s
 //     [n] (key in B order), perm [n] (A index of the cell at each B
 //     position), tmp [n] u64 (id << 32 | A index, scattered by key),
