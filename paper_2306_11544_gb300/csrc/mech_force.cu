@@ -295,10 +295,11 @@ __device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, 
 // memory (L1-cached).  Candidate order: (dz, dy) rows, then voxel order.  The
 // occupancy bits of all nine rows are fetched first (independent loads), so
 // a cell with few or no neighbours costs one round of memory latency, not nine.
-// Candidates are tested on the hi parts; a pair that passes is evaluated from
-// hi + lo.
+// A cell alone in its voxel leaves that voxel out (it holds only the skipped
+// self pair), so an isolated cell walks no run at all.  Candidates are tested
+// on the hi parts; a pair that passes is evaluated from hi + lo.
 __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, uint32_t q,
-                                              const float4 pi, const float4 qi, Acc3& acc) {
+                                              bool alone, const float4 pi, const float4 qi, Acc3& acc) {
     const float A = a.A_f;
     const int jx0 = c.ix > 0 ? c.ix - 1 : 0;
     const int jx1 = c.ix + 1 < g.n[0] ? c.ix + 1 : g.n[0] - 1;
@@ -315,6 +316,7 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
             occ9 |= (w & wmask) << (3 * p);
         }
     }
+    if (alone) occ9 &= ~(1u << (12 + (c.ix - jx0)));  // own voxel: row (dz, dy) = (0, 0) is row 4
     const float4 li = record_lo(pi, qi, g.qs);
     const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
     acc.zero();
@@ -364,9 +366,11 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
         uint32_t q = 0, nkey = 0, ntile = 0;
         if (valid) {
             uint32_t key;
+            bool alone = false;
             if (a.use_tiles) {
                 const uint2 e = a.slist[idx];
-                q = e.x;
+                q = e.x & 0x7FFFFFFFu;
+                alone = (e.x >> 31) != 0u;
                 key = e.y;
             } else {
                 q = idx;
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(key, g);
             Acc3 acc;
-            velocity_walk(a, g, c, q, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
+            velocity_walk(a, g, c, q, alone, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
             int nix, niy, niz;
             nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
@@ -433,11 +437,13 @@ __global__ void k_tile_classify(const StepArgs a) {
 // ------------------------------------------------------ sparse list ----
 // After the tile kernel (which may hand tiles back): B position and voxel key
 // of every cell whose tile is not dense, in runs of a warp's 32 consecutive
-// cells.
+// cells, and whether the cell is alone in its voxel (its sorted neighbours
+// q - 1 and q + 1 have other keys).
 __global__ void k_sparse_list(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;  // above every voxel key
     for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
         const uint32_t q = base + lane;
         bool sparse = false;
@@ -449,11 +455,16 @@ __global__ void k_sparse_list(const StepArgs a) {
             const Cell3 c = decode(k, g);
             sparse = !a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)];
         }
+        uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, k, 1);
+        uint32_t kn = __shfl_down_sync(0xFFFFFFFFu, k, 1);
+        if (lane == 0) kp = (q > 0u && q < a.n) ? a.vkey_s[q - 1u] : kNone;
+        if (lane == 31u || q + 1u >= a.n) kn = q + 1u < a.n ? a.vkey_s[q + 1u] : kNone;
+        const uint32_t alone = (kp != k && kn != k) ? 0x80000000u : 0u;
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, sparse);
         uint32_t off = 0;
         if (lane == 0 && m) off = atomicAdd(a.nsparse, (uint32_t)__popc(m));
         off = __shfl_sync(0xFFFFFFFFu, off, 0);
-        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = make_uint2(q, k);
+        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = make_uint2(q | alone, k);
     }
 }
 

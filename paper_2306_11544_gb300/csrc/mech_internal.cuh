@@ -172,7 +172,8 @@ struct StepArgs {
     uint8_t* tdense;
     uint32_t* tlist;
     uint32_t* ndense;
-    uint2* slist;          // {B position, voxel key} of the cells outside dense tiles
+    uint2* slist;          // {B position | alone << 31, voxel key} of the cells outside dense tiles
+                           // (alone: no other cell in its voxel)
     uint32_t* nsparse;
     float cut_eps;         // candidate-test margin for FP32 rounding (added to each grid's qm)
     unsigned long long wait_ns;  // time limit of every device-side wait
