@@ -494,7 +494,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     if (rc == MECH_OK) rc = h->alloc(&h->d_cca64, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_key, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_slist, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_nsparse, 1);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_nsparse, 2);
     if (rc == MECH_OK) rc = h->alloc(&h->d_stats, 2);
     if (rc == MECH_OK) rc = h->alloc(&h->d_vkey_s, np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_perm, np);

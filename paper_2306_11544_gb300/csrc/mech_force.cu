@@ -4,10 +4,11 @@
 // Mixed precision modes run four launches per step:
 //   k_tile_classify   flags every voxel tile (TX x TY x TZ voxels) holding at
 //                     least `dense_min` cells and lists the flagged tiles;
-//   k_force_tile      one CTA per dense tile: the rows of the tile's halo
-//                     (one voxel around it) are contiguous runs of the
-//                     voxel-sorted force records, so each row is staged into
-//                     shared memory by one TMA bulk copy; then one thread per
+//   k_force_tile      one CTA per dense tile (CTAs claim tiles one at a time
+//                     from a cursor): the rows of the tile's halo (one voxel
+//                     around it) are contiguous runs of the voxel-sorted
+//                     force records, so each row is staged into shared
+//                     memory by one TMA bulk copy; then one thread per
 //                     target cell tests its 27-voxel neighbourhood there;
 //   k_sparse_list     lists the cells outside dense tiles;
 //   k_force_cells     one thread per listed cell (sparse regions), reading
@@ -353,13 +354,15 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
 
 // ------------------------------------------- thread-per-cell kernel ----
 // Every cell not owned by a dense tile: the cells listed by k_sparse_list, or
-// all cells when tiles are off.
+// all cells when tiles are off.  (Claiming 32 listed cells at a time from a
+// cursor instead of the static grid-stride assignment measured slower: the
+// claim's round trip lengthens every iteration of this latency-bound loop.)
 template <int MODE>
 __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t total = a.use_tiles ? *a.nsparse : a.n;
+    const uint32_t total = a.use_tiles ? a.nsparse[0] : a.n;
     for (uint32_t base = warp * 32u; base < total; base += nwarps * 32u) {
         const uint32_t idx = base + lane;
         const bool valid = idx < total;
@@ -408,7 +411,10 @@ __global__ void k_tile_classify(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.nsparse = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.nsparse[0] = 0u;  // sparse-list length
+        a.nsparse[1] = 0u;  // tile cursor of the tile kernel
+    }
     for (uint32_t base = warp * 32u; base < a.ntiles; base += nwarps * 32u) {
         const uint32_t t = base + lane;
         const bool valid = t < a.ntiles;
@@ -536,6 +542,7 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
     __shared__ uint8_t s_tvox[kTCap];           // core voxel of each target (< 128)
     __shared__ int s_flag;                       // copy timeout
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_next;                  // next tile claimed by this CTA
 
     const int tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
@@ -549,7 +556,15 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
     __syncthreads();
     uint32_t phase = 0;
     const uint32_t ndense = *a.ndense;
-    for (uint32_t it = blockIdx.x; it < ndense; it += gridDim.x) {
+    // tiles are claimed one at a time from a cursor (their cost varies with
+    // their cell count), the claim's barrier also ending the previous tile:
+    // its shared tables and records are reused by the next one
+    auto claim = [&]() -> uint32_t {
+        if (tid == 0) s_next = atomicAdd(&a.nsparse[1], 1u);
+        __syncthreads();
+        return s_next;
+    };
+    for (uint32_t it = claim(); it < ndense; it = claim()) {
         const uint32_t tile = a.tlist[it];
         const int r = rep_of_tile(a.grids, a.nrep, tile);
         const GridDev& g = a.grids[r];
@@ -716,7 +731,6 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
             }
             next_step_counts(a, q, nkey, ntile, valid);
         }
-        __syncthreads();  // shared tables and records are reused by the next tile
     }
 }
 

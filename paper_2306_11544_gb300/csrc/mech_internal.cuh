@@ -174,7 +174,8 @@ struct StepArgs {
     uint32_t* ndense;
     uint2* slist;          // {B position | alone << 31, voxel key} of the cells outside dense tiles
                            // (alone: no other cell in its voxel)
-    uint32_t* nsparse;
+    uint32_t* nsparse;     // [0] sparse-list length, [1] tile cursor of the tile kernel
+                           // (both zeroed by k_tile_classify)
     float cut_eps;         // candidate-test margin for FP32 rounding (added to each grid's qm)
     unsigned long long wait_ns;  // time limit of every device-side wait
     uint32_t fault;        // host-armed fault injection (kFault* bits)
