@@ -73,8 +73,9 @@ def parse():
                    help="internal voxel side: a number, 'min' (2 A max R, the smallest valid) or 'user' (the workload's)")
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--graph", type=int, default=0)
-    p.add_argument("--tile", default="4,4,8", help="voxel tile for dense regions (4,4,4 or 4,4,8), or 0 for none")
-    p.add_argument("--dense-min", type=int, default=48)
+    p.add_argument("--tile", default="4,4,4",
+                   help="voxel tile for dense regions (4,4,4, 4,4,8 or 8,4,4), or 0 for none")
+    p.add_argument("--dense-min", type=int, default=12)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")

@@ -45,13 +45,15 @@ def workload_key(n_cells: int, cells_per_um3: float, mode: int) -> str:
 
 def candidates(min_voxel: float, user_voxel: float):
     """Settings tried: voxel sides from the smallest valid one up to the user's,
-    three tile shapes and no tiles, two density thresholds, two block sizes."""
+    three tile shapes (two density thresholds for two of them) and no tiles,
+    two block sizes."""
     up = lambda v: math.ceil(v * 1e4) / 1e4  # round up: never below the smallest valid side
     sides = sorted({up(min_voxel * f) for f in (1.0, 1.04, 1.1)} | {up(user_voxel)})
     sides = [s for s in sides if s <= max(up(user_voxel), up(min_voxel))]
     out = []
     for h in sides:
-        for tile, dmin in (((4, 4, 8), 48), ((4, 4, 8), 96), ((8, 4, 4), 48), ((4, 4, 4), 32), (None, 0)):
+        for tile, dmin in (((4, 4, 4), 12), ((4, 4, 4), 24), ((8, 4, 4), 16), ((4, 4, 8), 16), ((4, 4, 8), 48),
+                           (None, 0)):
             for block in (128, 256):
                 out.append({"voxel": h, "tile": tile, "dense_min": dmin, "block": block})
     return out

@@ -87,7 +87,7 @@ def test_clustered_20m_sampled_cells_against_oracle():
 
 def test_clustered_20m_mixed_modes_over_200_steps():
     """The 20M-cell configuration over its own 200 steps in the bench's launch
-    configuration (smallest internal voxel, 4x4x8 tiles, dense from 48 cells):
+    configuration (smallest internal voxel, 4x4x4 tiles, dense from 12 cells):
     both FP32 modes end within 1e-3 um of the FP64 mode, whose steps are the
     oracle's operations."""
     pop = synth.clustered_20m(seed=0)
@@ -98,7 +98,7 @@ def test_clustered_20m_mixed_modes_over_200_steps():
     errs = {}
     for mode in ("mixed", "kahan"):
         with H.make(pop, mode, voxel=hmin) as m:
-            m.set_tiling((4, 4, 8), 48)
+            m.set_tiling((4, 4, 4), 12)
             m.step(pop.steps)
             errs[mode] = float(np.abs(m.positions() - xr).max())
     print(f"clustered_20m, {pop.steps} steps, max |x - x_fp64| (um): {errs}")
