@@ -132,7 +132,7 @@ MECH_API int mech_set_launch(mech_t* h, int32_t force_block);
  * Voxel tiles (autotuner knob): dense regions are processed one tile of
  * tile_x * tile_y * tile_z voxels at a time, with the tile's halo staged in
  * shared memory; a tile holding at least dense_min cells is dense.  Supported
- * tiles: 4x4x4 (the default, dense_min 32), 4x4x8 and 8x4x4; (0, 0, 0) sends
+ * tiles: 4x4x4 (the default, dense_min 12), 4x4x8 and 8x4x4; (0, 0, 0) sends
  * every cell through the thread-per-cell kernel.  The FP32 summation order does not
  * depend on this setting.
  */

@@ -74,7 +74,7 @@ struct mech {
     // voxel tiles
     int ltx = 2, lty = 2, ltz = 2;
     bool use_tiles = true;
-    uint32_t dense_min = 32;
+    uint32_t dense_min = 12;
     uint32_t NT = 0;
     size_t tcap = 0;
     uint32_t* d_tcount[2] = {nullptr, nullptr};

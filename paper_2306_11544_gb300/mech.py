@@ -200,7 +200,7 @@ def mech_set_launch(h, force_block):
     _check(load_library().mech_set_launch(h, int(force_block)), "mech_set_launch")
 
 
-def mech_set_tiling(h, tile=(4, 4, 4), dense_min=32):
+def mech_set_tiling(h, tile=(4, 4, 4), dense_min=12):
     tx, ty, tz = (0, 0, 0) if tile is None else tile
     _check(load_library().mech_set_tiling(h, int(tx), int(ty), int(tz), int(dense_min)), "mech_set_tiling")
 
@@ -389,7 +389,7 @@ class Mech:
     def set_launch(self, block):
         mech_set_launch(self.h, block)
 
-    def set_tiling(self, tile=(4, 4, 4), dense_min=32):
+    def set_tiling(self, tile=(4, 4, 4), dense_min=12):
         mech_set_tiling(self.h, tile, dense_min)
 
     def set_stream(self, stream):
