@@ -199,6 +199,36 @@ MECH_API int mech_read_state(mech_t* h, double* xyz, double* vprev, double* comp
 MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const double* comp, int64_t step);
 
 /*
+ * Dynamic population (the cell count of a single-population handle changes
+ * between steps, as cells divide and die).  Both calls are ordered after the
+ * work already enqueued on the handle's stream and return when done; the
+ * next step bins the new population (keys are recomputed from the
+ * positions), and the handle's step count is unchanged.
+ *
+ * mech_remove_cells: alive holds n bytes in caller order; the cells with
+ * alive[i] == 0 are removed.  The survivors keep their relative order and are
+ * renumbered 0 .. n'-1 (caller index i becomes the number of survivors
+ * before it) with their whole state: position (and Kahan compensation),
+ * previous velocity, radius and coefficients.  The device work is two prefix
+ * sums and a compaction; nothing changes when every cell is alive.
+ *
+ * mech_add_cells: appends m cells with caller indices n .. n+m-1, positions
+ * xyz (3m doubles), radii, coefficients and types as in mech_create; their
+ * previous velocity is zero (their AB2 starts as at creation).  When n + m
+ * exceeds the device capacity, every per-cell buffer grows to max(n + m,
+ * 1.5 n) cells (one copy of the state).  A radius for which the handle's
+ * voxel (or internal voxel) is too small fails with MECH_E_VOXEL_TOO_SMALL
+ * and non-finite or invalid cells with MECH_E_NONFINITE / MECH_E_ARG, before
+ * anything changes.
+ *
+ * Both fail with MECH_E_ARG on batch handles (more than one replicate) and
+ * with MECH_E_STATE on a handle a device error left inconsistent.
+ */
+MECH_API int mech_remove_cells(mech_t* h, const uint8_t* alive);
+MECH_API int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr,
+                            const double* cca, const int32_t* type);
+
+/*
  * Binning of the current positions, for inspection (steps 1 of the update,
  * without advancing): key (n, caller order), count (V), start (V + 1) and
  * order (n: caller index of the cell at each sorted position), V = total

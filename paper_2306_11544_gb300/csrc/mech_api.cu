@@ -101,6 +101,13 @@ struct mech {
     uint32_t* d_occ = nullptr;
     size_t vcap = 0;  // capacity (entries) of count/start
     double* d_io = nullptr;  // 6n doubles of staging
+    // mech_remove_cells scratch (allocated at first use): alive bytes, scan
+    // flags, two prefix arrays and the scan's block sums, for ccap cells
+    uint8_t* d_alive = nullptr;
+    uint32_t* d_cflags = nullptr;
+    uint32_t* d_cpref[2] = {nullptr, nullptr};
+    uint32_t* d_cbsum = nullptr;
+    size_t ccap = 0;
     float* d_vout_f = nullptr;
     double* d_vout_d = nullptr;
     bool vout_valid = false;
@@ -437,6 +444,167 @@ int validate_cells(int64_t n, const double* xyz, const double* R, const double* 
     return MECH_OK;
 }
 
+// Per-cell device buffers of a capacity of np cells (the SoA component
+// stride): both state buffers, FP64 parameters in caller order, binning
+// scratch, staging and velocities-only outputs.
+struct CellBuffers {
+    StateBuf st[2] = {};
+    double* R64 = nullptr;
+    double* ccr64 = nullptr;
+    double* cca64 = nullptr;
+    uint32_t* key = nullptr;
+    uint2* slist = nullptr;
+    uint32_t* vkey_s = nullptr;
+    uint32_t* perm = nullptr;
+    unsigned long long* tmp = nullptr;
+    double* io = nullptr;
+    float* vout_f = nullptr;
+    double* vout_d = nullptr;
+};
+
+int alloc_cell_buffers(mech_t* h, size_t np, CellBuffers& b) {
+    b = CellBuffers{};
+    int rc = MECH_OK;
+    for (int s = 0; s < 2 && rc == MECH_OK; ++s) {
+        StateBuf& x = b.st[s];
+        rc = h->alloc(&x.pos64, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&x.posf, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&x.comp, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&x.vp64, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&x.vpf, 3 * np);
+        if (rc == MECH_OK) rc = h->alloc(&x.id, np);
+        if (rc == MECH_OK) rc = h->alloc(&x.rec, 2 * np);
+    }
+    if (rc == MECH_OK) rc = h->alloc(&b.R64, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.ccr64, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.cca64, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.key, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.slist, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.vkey_s, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.perm, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.tmp, np);
+    if (rc == MECH_OK) rc = h->alloc(&b.io, 6 * np);
+    if (rc == MECH_OK) rc = h->alloc(&b.vout_f, 3 * np);
+    if (rc == MECH_OK) rc = h->alloc(&b.vout_d, 3 * np);
+    return rc;
+}
+
+// Frees what alloc_cell_buffers allocated (null pointers are skipped).
+void free_cell_buffers(mech_t* h, const CellBuffers& b, size_t np) {
+    for (int s = 0; s < 2; ++s) {
+        const StateBuf& x = b.st[s];
+        h->free_ptr(x.pos64, 3 * np * 8);
+        h->free_ptr(x.posf, 3 * np * 4);
+        h->free_ptr(x.comp, 3 * np * 4);
+        h->free_ptr(x.vp64, 3 * np * 8);
+        h->free_ptr(x.vpf, 3 * np * 4);
+        h->free_ptr(x.id, np * 4);
+        h->free_ptr(x.rec, 2 * np * sizeof(float4));
+    }
+    h->free_ptr(b.R64, np * 8);
+    h->free_ptr(b.ccr64, np * 8);
+    h->free_ptr(b.cca64, np * 8);
+    h->free_ptr(b.key, np * 4);
+    h->free_ptr(b.slist, np * sizeof(uint2));
+    h->free_ptr(b.vkey_s, np * 4);
+    h->free_ptr(b.perm, np * 4);
+    h->free_ptr(b.tmp, np * 8);
+    h->free_ptr(b.io, 6 * np * 8);
+    h->free_ptr(b.vout_f, 3 * np * 4);
+    h->free_ptr(b.vout_d, 3 * np * 8);
+}
+
+CellBuffers cell_buffers_of(const mech_t* h) {
+    CellBuffers b;
+    b.st[0] = h->st[0];
+    b.st[1] = h->st[1];
+    b.R64 = h->d_R64;
+    b.ccr64 = h->d_ccr64;
+    b.cca64 = h->d_cca64;
+    b.key = h->d_key;
+    b.slist = h->d_slist;
+    b.vkey_s = h->d_vkey_s;
+    b.perm = h->d_perm;
+    b.tmp = h->d_tmp;
+    b.io = h->d_io;
+    b.vout_f = h->d_vout_f;
+    b.vout_d = h->d_vout_d;
+    return b;
+}
+
+void set_cell_buffers(mech_t* h, const CellBuffers& b) {
+    h->st[0] = b.st[0];
+    h->st[1] = b.st[1];
+    h->d_R64 = b.R64;
+    h->d_ccr64 = b.ccr64;
+    h->d_cca64 = b.cca64;
+    h->d_key = b.key;
+    h->d_slist = b.slist;
+    h->d_vkey_s = b.vkey_s;
+    h->d_perm = b.perm;
+    h->d_tmp = b.tmp;
+    h->d_io = b.io;
+    h->d_vout_f = b.vout_f;
+    h->d_vout_d = b.vout_d;
+}
+
+// Moves the per-cell buffers to a capacity of cap2 >= n cells: the current
+// state (SoA rows re-strided), ids, records and FP64 parameters are copied;
+// the other state buffer and the scratch need no copy (keys are recomputed).
+int grow_capacity(mech_t* h, size_t cap2) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const size_t np = h->npad, n = (size_t)h->n;
+    const CellBuffers old = cell_buffers_of(h);
+    CellBuffers nb;
+    const int rc = alloc_cell_buffers(h, cap2, nb);
+    if (rc != MECH_OK) {
+        free_cell_buffers(h, nb, cap2);
+        return rc;
+    }
+    if (n > 0) {
+        const StateBuf& so = old.st[h->cur];
+        const StateBuf& sn = nb.st[h->cur];
+        auto rows3 = [&](void* dst, const void* src, size_t es) {
+            return cudaMemcpy2DAsync(dst, cap2 * es, src, np * es, n * es, 3, cudaMemcpyDeviceToDevice, h->stream);
+        };
+        auto flat = [&](void* dst, const void* src, size_t bytes) {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        };
+        cudaError_t e = rows3(sn.pos64, so.pos64, 8);
+        if (e == cudaSuccess) e = rows3(sn.posf, so.posf, 4);
+        if (e == cudaSuccess) e = rows3(sn.comp, so.comp, 4);
+        if (e == cudaSuccess) e = rows3(sn.vp64, so.vp64, 8);
+        if (e == cudaSuccess) e = rows3(sn.vpf, so.vpf, 4);
+        if (e == cudaSuccess) e = flat(sn.id, so.id, n * 4);
+        if (e == cudaSuccess) e = flat(sn.rec, so.rec, 2 * n * sizeof(float4));
+        if (e == cudaSuccess) e = flat(nb.R64, old.R64, n * 8);
+        if (e == cudaSuccess) e = flat(nb.ccr64, old.ccr64, n * 8);
+        if (e == cudaSuccess) e = flat(nb.cca64, old.cca64, n * 8);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            free_cell_buffers(h, nb, cap2);
+            return fail(MECH_E_CUDA, std::string("capacity growth: ") + cudaGetErrorString(e));
+        }
+    }
+    set_cell_buffers(h, nb);
+    free_cell_buffers(h, old, np);
+    h->npad = (uint32_t)cap2;
+    h->keys_valid = false;
+    h->vout_valid = false;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+// Bookkeeping after the cell count changed.
+void set_cell_count(mech_t* h, int64_t n) {
+    h->n = n;
+    h->counts[0] = n;
+    h->elem_grid = (int)std::min<int64_t>(std::max<int64_t>(h->sms * 8, (n + 1023) / 1024), 1 << 20);
+    h->keys_valid = false;
+    h->vout_valid = false;
+    h->invalidate_graphs();
+}
+
 int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double* xyz, const double* R,
                 const double* ccr, const double* cca) {
     int64_t n = 0;
@@ -478,30 +646,11 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     for (int64_t i = 0; i < n; ++i) h->maxR = std::max(h->maxR, R[i]);
 
     const size_t np = h->npad;
-    int rc = MECH_OK;
-    for (int s = 0; s < 2 && rc == MECH_OK; ++s) {
-        StateBuf& b = h->st[s];
-        rc = h->alloc(&b.pos64, 3 * np);
-        if (rc == MECH_OK) rc = h->alloc(&b.posf, 3 * np);
-        if (rc == MECH_OK) rc = h->alloc(&b.comp, 3 * np);
-        if (rc == MECH_OK) rc = h->alloc(&b.vp64, 3 * np);
-        if (rc == MECH_OK) rc = h->alloc(&b.vpf, 3 * np);
-        if (rc == MECH_OK) rc = h->alloc(&b.id, np);
-        if (rc == MECH_OK) rc = h->alloc(&b.rec, 2 * np);
-    }
-    if (rc == MECH_OK) rc = h->alloc(&h->d_R64, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_ccr64, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_cca64, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_key, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_slist, np);
+    CellBuffers cb;
+    int rc = alloc_cell_buffers(h, np, cb);
+    set_cell_buffers(h, cb);
     if (rc == MECH_OK) rc = h->alloc(&h->d_nsparse, 2);
     if (rc == MECH_OK) rc = h->alloc(&h->d_stats, 2);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_vkey_s, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_perm, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_tmp, np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_io, 6 * np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_vout_f, 3 * np);
-    if (rc == MECH_OK) rc = h->alloc(&h->d_vout_d, 3 * np);
     if (rc == MECH_OK) rc = h->alloc(&h->d_err, 1);
     if (rc == MECH_OK) rc = h->alloc(&h->d_ndense, 1);
     if (rc != MECH_OK) return bail(rc);
@@ -881,6 +1030,124 @@ int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const dou
     h->vout_valid = false;
     h->poisoned = false;
     return MECH_OK;
+}
+
+int mech_remove_cells(mech_t* h, const uint8_t* alive) {
+    MECH_TRY(check_handle(h));
+    if (h->nrep != 1) return fail(MECH_E_ARG, "mech_remove_cells: single-population handles only");
+    if (h->poisoned)
+        return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
+    const uint32_t n = (uint32_t)h->n;
+    if (n == 0) return MECH_OK;
+    if (!alive) return fail(MECH_E_ARG, "null alive mask");
+    // scratch for the two prefix sums (padded to the scan's tile)
+    const size_t need = ((size_t)h->npad + kScanTile - 1) / kScanTile * kScanTile;
+    if (h->ccap < need) {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->free_ptr(h->d_alive, h->ccap);
+        h->free_ptr(h->d_cflags, h->ccap * 4);
+        h->free_ptr(h->d_cpref[0], h->ccap * 4);
+        h->free_ptr(h->d_cpref[1], h->ccap * 4);
+        h->free_ptr(h->d_cbsum, (h->ccap / kScanTile + 1) * 4);
+        h->d_alive = nullptr;
+        h->d_cflags = h->d_cpref[0] = h->d_cpref[1] = h->d_cbsum = nullptr;
+        h->ccap = 0;
+        int rc = h->alloc(&h->d_alive, need);
+        if (rc == MECH_OK) rc = h->alloc(&h->d_cflags, need);
+        if (rc == MECH_OK) rc = h->alloc(&h->d_cpref[0], need);
+        if (rc == MECH_OK) rc = h->alloc(&h->d_cpref[1], need);
+        if (rc == MECH_OK) rc = h->alloc(&h->d_cbsum, need / kScanTile + 1);
+        if (rc != MECH_OK) return rc;
+        h->ccap = need;
+    }
+    const uint32_t pad = (uint32_t)(((size_t)n + kScanTile - 1) / kScanTile * kScanTile);
+    StepArgs a = h->args(h->cur, 1);
+    uint32_t* newid = h->d_cpref[0];
+    uint32_t* dst = h->d_cpref[1];
+    // new caller index of each survivor: exclusive prefix of the alive flags
+    CUDA_TRY(cudaMemcpyAsync(h->d_alive, alive, n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(launch_alive_flags(h->d_alive, n, pad, h->d_cflags, h->stream));
+    CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, newid, nullptr, nullptr, h->stream));
+    uint32_t last[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(&last[0], newid + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&last[1], h->d_cflags + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const uint32_t n2 = last[0] + last[1];
+    if (n2 == n) return MECH_OK;
+    // new slot of each surviving slot: exclusive prefix of the keep flags in
+    // state order (the survivors keep their voxel order)
+    CUDA_TRY(launch_keep_flags(a, h->st[h->cur], h->d_alive, pad, h->d_cflags, h->stream));
+    CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, dst, nullptr, nullptr, h->stream));
+    CUDA_TRY(launch_compact_state(a, h->d_alive, dst, newid, h->stream));
+    CUDA_TRY(launch_compact_params(a, h->d_alive, newid, h->d_io, h->stream));
+    const size_t np = h->npad;
+    if (n2 > 0) {
+        CUDA_TRY(cudaMemcpyAsync(h->d_R64, h->d_io, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(h->d_ccr64, h->d_io + np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(h->d_cca64, h->d_io + 2 * np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    h->cur ^= 1;
+    set_cell_count(h, n2);
+    return mech_sync(h);
+}
+
+int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr, const double* cca,
+                   const int32_t* type) {
+    (void)type;
+    MECH_TRY(check_handle(h));
+    if (h->nrep != 1) return fail(MECH_E_ARG, "mech_add_cells: single-population handles only");
+    if (h->poisoned)
+        return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
+    if (m < 0) return fail(MECH_E_ARG, "negative cell count");
+    if (m == 0) return MECH_OK;
+    MECH_TRY(validate_cells(m, xyz, R, ccr, cca));
+    if (h->n + m >= (int64_t)0x7FFFFFFF) return fail(MECH_E_ARG, "more than 2^31-1 cells");
+    double maxR = h->maxR;
+    for (int64_t i = 0; i < m; ++i) maxR = std::max(maxR, R[i]);
+    if (h->params_set && maxR > h->maxR) {
+        if (h->voxel_user < 2.0 * h->A * maxR)
+            return fail(MECH_E_VOXEL_TOO_SMALL, "a new radius needs voxel_size >= 2 A max R = " +
+                                                    std::to_string(2.0 * h->A * maxR));
+        if (h->voxel_int > 0.0 && h->voxel_int < 2.0 * h->A * maxR * (1.0 + 1e-6))
+            return fail(MECH_E_VOXEL_TOO_SMALL, "a new radius needs an internal voxel >= 2 A max R (1 + 1e-6)");
+    }
+    const int64_t n = h->n;
+    if ((size_t)(n + m) > (size_t)h->npad) {
+        const size_t cap2 = (size_t)(std::max<int64_t>(n + m, n + n / 2) + 63) / 64 * 64;
+        MECH_TRY(grow_capacity(h, cap2));
+    }
+    // records (radius + residual, coefficient roots; the position fields are
+    // written by the next canonicalisation), ids n .. n+m-1, parameters
+    std::vector<uint32_t> ids(m);
+    std::vector<float4> rec(2 * m);
+    for (int64_t i = 0; i < m; ++i) {
+        ids[i] = (uint32_t)(n + i);
+        const float Rf = (float)R[i];
+        int e2 = 0;
+        std::frexp(Rf, &e2);
+        const double units = (R[i] - (double)Rf) / std::ldexp(1.0, e2 - 24);
+        const long L = std::lround(std::min(32767.0, std::max(-32768.0, units * 32768.0)));
+        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
+        float wzf, wxyf;
+        const uint32_t wxy = 0x80008000u;
+        std::memcpy(&wzf, &wzr, 4);
+        std::memcpy(&wxyf, &wxy, 4);
+        rec[2 * i] = make_float4(0.f, 0.f, 0.f, Rf);
+        rec[2 * i + 1] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), wxyf, wzf);
+    }
+    const StateBuf& s = h->st[h->cur];
+    cudaStream_t st = h->stream;
+    CUDA_TRY(cudaMemcpyAsync(s.id + n, ids.data(), m * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s.rec + 2 * n, rec.data(), 2 * m * sizeof(float4), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_R64 + n, R, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_ccr64 + n, ccr, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_cca64 + n, cca, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz, 3 * m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_append_state(h->args(h->cur, 1), s, h->d_io, (uint32_t)n, (uint32_t)m, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above are released on return
+    h->maxR = maxR;
+    set_cell_count(h, n + m);
+    return mech_sync(h);
 }
 
 int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order) {

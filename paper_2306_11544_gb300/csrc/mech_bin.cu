@@ -308,6 +308,85 @@ __global__ void k_load_pos(const StepArgs a, const StateBuf st, const double* __
     }
 }
 
+// ---- dynamic population ----
+__global__ void k_alive_flags(const uint8_t* __restrict__ alive, uint32_t n, uint32_t pad, uint32_t* __restrict__ flags) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < pad; i += stride)
+        flags[i] = (i < n && alive[i] != 0) ? 1u : 0u;
+}
+
+__global__ void k_keep_flags(const StepArgs a, const StateBuf st, const uint8_t* __restrict__ alive, uint32_t pad,
+                             uint32_t* __restrict__ flags) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < pad; q += stride) {
+        uint32_t f = 0u;
+        if (q < a.n) {
+            const uint32_t id = st.id[q];
+            if (id < a.n) f = alive[id] != 0 ? 1u : 0u;
+            else atomicOr(a.err, kErrIndex);  // only after an earlier device error
+        }
+        flags[q] = f;
+    }
+}
+
+__global__ void k_compact_state(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ dst,
+                                const uint32_t* __restrict__ newid) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = a.A.id[q];
+        if (id >= a.n) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        if (!alive[id]) continue;
+        const uint32_t f = dst[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            a.B.pos64[d * np + f] = a.A.pos64[d * np + q];
+            a.B.posf[d * np + f] = a.A.posf[d * np + q];
+            a.B.comp[d * np + f] = a.A.comp[d * np + q];
+            a.B.vp64[d * np + f] = a.A.vp64[d * np + q];
+            a.B.vpf[d * np + f] = a.A.vpf[d * np + q];
+        }
+        a.B.rec[2 * (size_t)f] = a.A.rec[2 * (size_t)q];
+        a.B.rec[2 * (size_t)f + 1] = a.A.rec[2 * (size_t)q + 1];
+        a.B.id[f] = newid[id];
+    }
+}
+
+__global__ void k_compact_params(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ newid,
+                                 double* __restrict__ io) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        if (!alive[i]) continue;
+        const uint32_t j = newid[i];
+        io[j] = a.R64[i];
+        io[np + j] = a.ccr64[i];
+        io[2 * np + j] = a.cca64[i];
+    }
+}
+
+__global__ void k_append_state(const StepArgs a, const StateBuf st, const double* __restrict__ io, uint32_t n0,
+                               uint32_t m) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const size_t q = (size_t)n0 + j;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = io[3 * (size_t)j + d];
+            const float xh = __double2float_rn(x);
+            st.pos64[d * np + q] = x;
+            st.posf[d * np + q] = xh;
+            st.comp[d * np + q] = __double2float_rn(__dsub_rn((double)xh, x));
+            st.vp64[d * np + q] = 0.0;
+            st.vpf[d * np + q] = 0.0f;
+        }
+    }
+}
+
 __global__ void k_load_vprev(const StepArgs a, const StateBuf st, const double* __restrict__ in) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
@@ -363,6 +442,38 @@ cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     k_canon_rank<<<grid, 256, 0, s>>>(a);
     k_canon_gather<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alive_flags(const uint8_t* alive, uint32_t n, uint32_t pad, uint32_t* flags, cudaStream_t s) {
+    k_alive_flags<<<elementwise_grid(pad), 256, 0, s>>>(alive, n, pad, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keep_flags(const StepArgs& a, const StateBuf& st, const uint8_t* alive, uint32_t pad,
+                              uint32_t* flags, cudaStream_t s) {
+    k_keep_flags<<<elementwise_grid(pad), 256, 0, s>>>(a, st, alive, pad, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
+                                 cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_compact_state<<<elementwise_grid(a.n), 256, 0, s>>>(a, alive, dst, newid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
+                                  cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_compact_params<<<elementwise_grid(a.n), 256, 0, s>>>(a, alive, newid, io);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, uint32_t n0, uint32_t m,
+                                cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    k_append_state<<<elementwise_grid(m), 256, 0, s>>>(a, st, io, n0, m);
     return cudaGetLastError();
 }
 

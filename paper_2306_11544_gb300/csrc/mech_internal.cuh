@@ -192,6 +192,28 @@ cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, ui
 cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);
+
+// ---- dynamic population, between steps (mech_api.cu: mech_remove_cells /
+// mech_add_cells) ----
+// flags[i] = (alive[i] != 0) for i < n, 0 for n <= i < pad (a scan input).
+cudaError_t launch_alive_flags(const uint8_t* alive, uint32_t n, uint32_t pad, uint32_t* flags, cudaStream_t s);
+// flags[q] = (alive[st.id[q]] != 0) in state order, 0 up to pad.
+cudaError_t launch_keep_flags(const StepArgs& a, const StateBuf& st, const uint8_t* alive, uint32_t pad,
+                              uint32_t* flags, cudaStream_t s);
+// Survivors of a.A move to a.B at dst[q] (exclusive prefix of the keep flags
+// over the state order) with caller index newid[id] (exclusive prefix of the
+// alive flags over the caller order); every state array is moved, whatever
+// the mode.
+cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
+                                 cudaStream_t s);
+// FP64 parameters of the survivors (caller order) into io[0..np), io[np..2np),
+// io[2np..3np) at their new caller index.
+cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
+                                  cudaStream_t s);
+// Cells n0 .. n0+m-1 of st: positions from io (3 doubles per cell, rounded as
+// by mech_write_positions), zero previous velocity.
+cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, uint32_t n0, uint32_t m,
+                                cudaStream_t s);
 cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const float* vf, const double* vd,
                                  double* out, cudaStream_t s);
 cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double* in, int raw_kahan,

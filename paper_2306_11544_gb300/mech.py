@@ -43,8 +43,8 @@ EXPORTS = [
     "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
-    "mech_load_state", "mech_debug_bins", "mech_pair_stats", "mech_bin_noalloc", "mech_debug_inject", "mech_info", "mech_grid",
-    "mech_destroy",
+    "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_debug_bins", "mech_pair_stats", "mech_bin_noalloc",
+    "mech_debug_inject", "mech_info", "mech_grid", "mech_destroy",
 ]
 
 
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
             "mech_write_positions": ([_P, _P], ctypes.c_int),
             "mech_read_state": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_load_state": ([_P, _P, _P, _P, ctypes.c_int64], ctypes.c_int),
+            "mech_remove_cells": ([_P, _P], ctypes.c_int),
+            "mech_add_cells": ([_P, ctypes.c_int64, _P, _P, _P, _P, _P], ctypes.c_int),
             "mech_debug_bins": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_pair_stats": ([_P, _P, _P], ctypes.c_int),
             "mech_bin_noalloc": ([ctypes.c_int64, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -163,6 +165,29 @@ def mech_create(n, xyz, R, ccr, cca, ctype=None):
     _check(lib.mech_create(ctypes.byref(h), int(n), _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), _ptr(t)),
            "mech_create")
     return h
+
+
+def mech_remove_cells(h, n, alive):
+    """Remove the cells whose alive flag is false (n flags, caller order);
+    returns the new cell count."""
+    a = np.ascontiguousarray(alive, dtype=np.uint8).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} flags, got {a.size}")
+    _check(load_library().mech_remove_cells(h, _ptr(a)), "mech_remove_cells")
+    return int(np.count_nonzero(a))
+
+
+def mech_add_cells(h, xyz, R, ccr, cca, ctype=None):
+    """Append cells (caller indices n .. n+m-1); returns m."""
+    xyz = _f64(xyz).reshape(-1)
+    m = xyz.size // 3
+    if xyz.size != 3 * m:
+        raise ValueError("xyz must hold 3 values per cell")
+    R, ccr, cca = _f64(R, m), _f64(ccr, m), _f64(cca, m)
+    t = None if ctype is None else np.ascontiguousarray(ctype, dtype=np.int32)
+    _check(load_library().mech_add_cells(h, int(m), _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), _ptr(t)),
+           "mech_add_cells")
+    return m
 
 
 def mech_create_batch(counts, xyz, R, ccr, cca, ctype=None):
@@ -427,6 +452,16 @@ class Mech:
 
     def load_state(self, state):
         mech_load_state(self.h, self.n, state)
+
+    def remove_cells(self, alive):
+        """Keep the cells whose flag is true; survivors are renumbered in order."""
+        self.n = mech_remove_cells(self.h, self.n, alive)
+        self.counts = np.array([self.n], dtype=np.int64)
+
+    def add_cells(self, xyz, R, ccr, cca, ctype=None):
+        """Append cells after the current ones (zero previous velocity)."""
+        self.n += mech_add_cells(self.h, xyz, R, ccr, cca, ctype)
+        self.counts = np.array([self.n], dtype=np.int64)
 
     def bins(self):
         return mech_debug_bins(self.h, self.n)
