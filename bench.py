@@ -89,6 +89,10 @@ def parse():
                         "configs 1, 2, 3 and 5; prints one JSON line")
     p.add_argument("--plain-loop", action="store_true",
                    help="ensembles: also time the plain single-population path looped over replicates")
+    p.add_argument("--turnover", type=float, default=0.0,
+                   help="single populations: also time a loop in which this fraction of the cells dies every "
+                        "--turnover-every steps and as many daughters are added next to random survivors")
+    p.add_argument("--turnover-every", type=int, default=10)
     return p.parse_args()
 
 
@@ -318,6 +322,52 @@ def oracle_timing(args):
     return 0
 
 
+def turnover_events(pop, n_events, frac, seed=12345):
+    """Precomputed death and division events that keep the cell count: each
+    event's alive mask (caller order at that time) and as many daughters, half
+    a radius from random survivors at their initial positions, with the
+    parents' radius and coefficients."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    orig = np.arange(pop.n)  # initial index of each current cell
+    events = []
+    for _ in range(n_events):
+        alive = rng.random(len(orig)) >= frac
+        orig = orig[alive]
+        r = int(len(alive) - alive.sum())
+        parents = orig[rng.integers(0, len(orig), size=r)]
+        u = rng.normal(size=(r, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        xyz = pop.xyz[parents] + 0.5 * pop.R[parents][:, None] * u
+        events.append((alive, xyz, pop.R[parents], pop.ccr[parents], pop.cca[parents]))
+        orig = np.concatenate([orig, parents])
+    return events
+
+
+def time_turnover(m, pop, args, stream, torch, ms_per_step_plain):
+    """The step loop with death and division every `turnover_every` steps
+    (mech_remove_cells + mech_add_cells, host calls between steps), timed on
+    the handle's stream like the main loop."""
+    every = max(1, args.turnover_every)
+    n_events = max(1, args.steps // every)
+    events = turnover_events(pop, n_events, args.turnover)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for alive, xyz, R, ccr, cca in events:
+        m.step(every)
+        m.remove_cells(alive)
+        m.add_cells(xyz, R, ccr, cca)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    steps = n_events * every
+    return {"fraction": args.turnover, "every": every, "events": n_events,
+            "cells_replaced_per_event": float(np.mean([len(e[0]) - e[0].sum() for e in events])),
+            "value": pop.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "ms_per_event": (ms - steps * ms_per_step_plain) / n_events,
+            "path": "mech_step(every) -> mech_remove_cells -> mech_add_cells (host calls between steps)"}
+
+
 def time_plain_loop(ens, args, stream, torch):
     """The plain single-population API looped over the replicates: one handle
     per replicate, each advanced `steps` steps on the same stream."""
@@ -531,6 +581,11 @@ def main():
         else:
             tests_method = tests_done
         stats = (tests_method, tests_done, pairs)
+    turnover = None
+    if args.turnover > 0 and not batched:
+        if args.voxel not in ("user", "0"):
+            m.set_internal_voxel(args.voxel_value)  # the step's own grid again
+        turnover = time_turnover(m, wl, args, stream, torch, t_max / args.steps)
     m.close()
 
     if rank != 0:
@@ -591,6 +646,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": info["launches_per_step"] * args.steps,
     }
+    if turnover is not None:
+        line["turnover"] = turnover
     if batched:
         line["batched"] = {"replicates": len(wl.reps), "graph_steps": args.graph,
                            "launches_per_step": info["launches_per_step"]}
