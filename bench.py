@@ -349,7 +349,14 @@ def time_turnover(m, pop, args, stream, torch, ms_per_step_plain):
     the handle's stream like the main loop."""
     every = max(1, args.turnover_every)
     n_events = max(1, args.steps // every)
-    events = turnover_events(pop, n_events, args.turnover)
+
+    def pinned(a):  # page-locked host copies, as a caller that moves data often would keep them
+        out = torch.empty(a.shape, dtype=getattr(torch, a.dtype.name), pin_memory=True).numpy()
+        out[...] = a
+        return out
+
+    events = [tuple(pinned(np.ascontiguousarray(x)) for x in (alive.astype(np.uint8), xyz, R, ccr, cca))
+              for alive, xyz, R, ccr, cca in turnover_events(pop, n_events, args.turnover)]
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -362,10 +369,11 @@ def time_turnover(m, pop, args, stream, torch, ms_per_step_plain):
     ms = ev0.elapsed_time(ev1)
     steps = n_events * every
     return {"fraction": args.turnover, "every": every, "events": n_events,
-            "cells_replaced_per_event": float(np.mean([len(e[0]) - e[0].sum() for e in events])),
+            "cells_replaced_per_event": float(np.mean([len(e[1]) for e in events])),
             "value": pop.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "ms_per_event": (ms - steps * ms_per_step_plain) / n_events,
-            "path": "mech_step(every) -> mech_remove_cells -> mech_add_cells (host calls between steps)"}
+            "path": "mech_step(every) -> mech_remove_cells -> mech_add_cells (host calls between steps, "
+                    "page-locked host arrays)"}
 
 
 def time_plain_loop(ens, args, stream, torch):

@@ -1116,35 +1116,15 @@ int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, con
         const size_t cap2 = (size_t)(std::max<int64_t>(n + m, n + n / 2) + 63) / 64 * 64;
         MECH_TRY(grow_capacity(h, cap2));
     }
-    // records (radius + residual, coefficient roots; the position fields are
-    // written by the next canonicalisation), ids n .. n+m-1, parameters
-    std::vector<uint32_t> ids(m);
-    std::vector<float4> rec(2 * m);
-    for (int64_t i = 0; i < m; ++i) {
-        ids[i] = (uint32_t)(n + i);
-        const float Rf = (float)R[i];
-        int e2 = 0;
-        std::frexp(Rf, &e2);
-        const double units = (R[i] - (double)Rf) / std::ldexp(1.0, e2 - 24);
-        const long L = std::lround(std::min(32767.0, std::max(-32768.0, units * 32768.0)));
-        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
-        float wzf, wxyf;
-        const uint32_t wxy = 0x80008000u;
-        std::memcpy(&wzf, &wzr, 4);
-        std::memcpy(&wxyf, &wxy, 4);
-        rec[2 * i] = make_float4(0.f, 0.f, 0.f, Rf);
-        rec[2 * i + 1] = make_float4((float)std::sqrt(ccr[i]), (float)std::sqrt(cca[i]), wxyf, wzf);
-    }
+    // parameters and positions; the kernel writes the records, ids and state
     const StateBuf& s = h->st[h->cur];
     cudaStream_t st = h->stream;
-    CUDA_TRY(cudaMemcpyAsync(s.id + n, ids.data(), m * 4, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(s.rec + 2 * n, rec.data(), 2 * m * sizeof(float4), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_R64 + n, R, m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_ccr64 + n, ccr, m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_cca64 + n, cca, m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz, 3 * m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(launch_append_state(h->args(h->cur, 1), s, h->d_io, (uint32_t)n, (uint32_t)m, st));
-    CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above are released on return
+    CUDA_TRY(cudaStreamSynchronize(st));  // the caller's arrays may be released on return
     h->maxR = maxR;
     set_cell_count(h, n + m);
     return mech_sync(h);

@@ -374,6 +374,20 @@ __global__ void k_append_state(const StepArgs a, const StateBuf st, const double
     const size_t np = a.npad;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
         const size_t q = (size_t)n0 + j;
+        // record: radius as FP32 plus its residual in units of ulp(R) / 2^15
+        // (16 bits, offset 2^15), coefficient square roots; the position
+        // fields are written by the next canonicalisation
+        const double R = a.R64[q];
+        const float Rf = __double2float_rn(R);
+        int e2 = 0;
+        frexpf(Rf, &e2);  // Rf = f 2^e2, f in [0.5, 1): ulp(Rf) = 2^(e2 - 24)
+        const double units = (R - (double)Rf) / ldexp(1.0, e2 - 24);
+        const long long L = llround(fmin(32767.0, fmax(-32768.0, units * 32768.0)));
+        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
+        st.rec[2 * q] = make_float4(0.f, 0.f, 0.f, Rf);
+        st.rec[2 * q + 1] = make_float4(__double2float_rn(sqrt(a.ccr64[q])), __double2float_rn(sqrt(a.cca64[q])),
+                                        __uint_as_float(0x80008000u), __uint_as_float(wzr));
+        st.id[q] = (uint32_t)q;  // caller order: appended cells take indices n0 .. n0+m-1
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double x = io[3 * (size_t)j + d];

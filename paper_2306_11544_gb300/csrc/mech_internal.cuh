@@ -210,8 +210,10 @@ cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const 
 // io[2np..3np) at their new caller index.
 cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
                                   cudaStream_t s);
-// Cells n0 .. n0+m-1 of st: positions from io (3 doubles per cell, rounded as
-// by mech_write_positions), zero previous velocity.
+// Cells n0 .. n0+m-1 of st (caller indices n0 .. n0+m-1): positions from io
+// (3 doubles per cell, rounded as by mech_write_positions), zero previous
+// velocity, force records from the FP64 parameters a.R64/ccr64/cca64 (already
+// in place at n0 .. n0+m-1).
 cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, uint32_t n0, uint32_t m,
                                 cudaStream_t s);
 cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const float* vf, const double* vd,
