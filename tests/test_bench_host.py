@@ -1,0 +1,38 @@
+"""Host logic of bench.py's turnover mode (no GPU): the precomputed death and
+division events keep the cell count, place each daughter half a radius from a
+survivor of that event, give it that cell's parameters, and are reproducible."""
+import numpy as np
+
+import bench
+from paper_2306_11544_gb300 import synth
+
+
+def replay(pop, events):
+    """Apply the events to the initial indices, as the handle sees them."""
+    orig = np.arange(pop.n)
+    out = []
+    for alive, xyz, R, ccr, cca in events:
+        assert len(alive) == len(orig) == pop.n  # the count is kept
+        orig = orig[alive]
+        # each daughter sits half a radius from one survivor of this event
+        d = np.linalg.norm(xyz[:, None, :] - pop.xyz[orig][None, :, :], axis=2)
+        j = np.argmin(np.abs(d - 0.5 * pop.R[orig][None, :]), axis=1)
+        parents = orig[j]
+        assert np.allclose(np.linalg.norm(xyz - pop.xyz[parents], axis=1), 0.5 * pop.R[parents])
+        assert np.array_equal(R, pop.R[parents]) and np.array_equal(ccr, pop.ccr[parents])
+        assert np.array_equal(cca, pop.cca[parents])
+        assert len(xyz) == pop.n - len(orig)  # as many daughters as deaths
+        out.append(len(xyz))
+        orig = np.concatenate([orig, parents])
+    return out
+
+
+def test_turnover_events_keep_the_count_and_follow_survivors():
+    pop = synth.spheroid_1m(seed=3, scale=0.0005)  # 500 cells, three types
+    events = bench.turnover_events(pop, 4, 0.05)
+    counts = replay(pop, events)
+    assert all(c > 0 for c in counts)
+    again = bench.turnover_events(pop, 4, 0.05)
+    for a, b in zip(events, again):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
