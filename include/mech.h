@@ -210,7 +210,8 @@ MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, 
  * renumbered 0 .. n'-1 (caller index i becomes the number of survivors
  * before it) with their whole state: position (and Kahan compensation),
  * previous velocity, radius and coefficients.  The device work is two prefix
- * sums and a compaction; nothing changes when every cell is alive.
+ * sums, survivors moved into the dead cells' slots and a compaction of the
+ * caller-order parameters; nothing changes when every cell is alive.
  *
  * mech_add_cells: appends m cells with caller indices n .. n+m-1, positions
  * xyz (3m doubles), radii, coefficients and types as in mech_create; their

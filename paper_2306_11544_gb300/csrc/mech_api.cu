@@ -1074,11 +1074,11 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     const uint32_t n2 = last[0] + last[1];
     if (n2 == n) return MECH_OK;
-    // new slot of each surviving slot: exclusive prefix of the keep flags in
-    // state order (the survivors keep their voxel order)
+    // survivors into slots [0, n2) in place: the keep flags' exclusive prefix
+    // in state order numbers the holes below n2 and the movers above it
     CUDA_TRY(launch_keep_flags(a, h->st[h->cur], h->d_alive, pad, h->d_cflags, h->stream));
     CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, dst, nullptr, nullptr, h->stream));
-    CUDA_TRY(launch_compact_state(a, h->d_alive, dst, newid, h->stream));
+    CUDA_TRY(launch_remove_in_place(a, h->d_alive, dst, newid, n2, h->d_cflags, h->stream));
     CUDA_TRY(launch_compact_params(a, h->d_alive, newid, h->d_io, h->stream));
     const size_t np = h->npad;
     if (n2 > 0) {
@@ -1086,7 +1086,6 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
         CUDA_TRY(cudaMemcpyAsync(h->d_ccr64, h->d_io + np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
         CUDA_TRY(cudaMemcpyAsync(h->d_cca64, h->d_io + 2 * np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
     }
-    h->cur ^= 1;
     set_cell_count(h, n2);
     return mech_sync(h);
 }

@@ -329,29 +329,67 @@ __global__ void k_keep_flags(const StepArgs a, const StateBuf st, const uint8_t*
     }
 }
 
-__global__ void k_compact_state(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ dst,
-                                const uint32_t* __restrict__ newid) {
+// Removal in place, in state order: the survivors end in slots [0, n2).  A
+// dead slot q < n2 is a hole, numbered q - keep_pref[q] (dead slots before
+// it); a surviving slot q >= n2 is a mover, numbered keep_pref[q] -
+// keep_pref[n2]; mover k fills hole k.  Holes and movers are disjoint, so the
+// moves need no second buffer, and only as many cells move as died below n2
+// (the next binning restores the voxel order).
+__global__ void k_list_holes(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ keep_pref,
+                             uint32_t n2, uint32_t* __restrict__ hole) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += stride) {
+        const uint32_t id = a.A.id[q];
+        if (id >= a.n) {  // only after an earlier device error
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        if (!alive[id]) hole[q - keep_pref[q]] = q;
+    }
+}
+
+__global__ void k_fill_holes(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ keep_pref,
+                             uint32_t n2, const uint32_t* __restrict__ hole) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const size_t np = a.npad;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+    const uint32_t base = keep_pref[n2];
+    for (uint32_t q = n2 + blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const uint32_t id = a.A.id[q];
         if (id >= a.n) {
             atomicOr(a.err, kErrIndex);
             continue;
         }
         if (!alive[id]) continue;
-        const uint32_t f = dst[q];
+        const uint32_t f = hole[keep_pref[q] - base];
+        if (f >= n2) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            a.B.pos64[d * np + f] = a.A.pos64[d * np + q];
-            a.B.posf[d * np + f] = a.A.posf[d * np + q];
-            a.B.comp[d * np + f] = a.A.comp[d * np + q];
-            a.B.vp64[d * np + f] = a.A.vp64[d * np + q];
-            a.B.vpf[d * np + f] = a.A.vpf[d * np + q];
+            a.A.pos64[d * np + f] = a.A.pos64[d * np + q];
+            a.A.posf[d * np + f] = a.A.posf[d * np + q];
+            a.A.comp[d * np + f] = a.A.comp[d * np + q];
+            a.A.vp64[d * np + f] = a.A.vp64[d * np + q];
+            a.A.vpf[d * np + f] = a.A.vpf[d * np + q];
         }
-        a.B.rec[2 * (size_t)f] = a.A.rec[2 * (size_t)q];
-        a.B.rec[2 * (size_t)f + 1] = a.A.rec[2 * (size_t)q + 1];
-        a.B.id[f] = newid[id];
+        a.A.rec[2 * (size_t)f] = a.A.rec[2 * (size_t)q];
+        a.A.rec[2 * (size_t)f + 1] = a.A.rec[2 * (size_t)q + 1];
+        a.A.id[f] = id;
+    }
+}
+
+// Caller indices of the survivors in slots [0, n2): their rank among the
+// survivors in caller order.
+__global__ void k_renumber(const StepArgs a, const uint32_t* __restrict__ newid, uint32_t n2) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += stride) {
+        const uint32_t id = a.A.id[q];
+        if (id >= a.n) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        a.A.id[q] = newid[id];
     }
 }
 
@@ -470,10 +508,13 @@ cudaError_t launch_keep_flags(const StepArgs& a, const StateBuf& st, const uint8
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
-                                 cudaStream_t s) {
+cudaError_t launch_remove_in_place(const StepArgs& a, const uint8_t* alive, const uint32_t* keep_pref,
+                                   const uint32_t* newid, uint32_t n2, uint32_t* hole, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    k_compact_state<<<elementwise_grid(a.n), 256, 0, s>>>(a, alive, dst, newid);
+    const int g = elementwise_grid(a.n);
+    k_list_holes<<<g, 256, 0, s>>>(a, alive, keep_pref, n2, hole);
+    k_fill_holes<<<g, 256, 0, s>>>(a, alive, keep_pref, n2, hole);
+    k_renumber<<<g, 256, 0, s>>>(a, newid, n2);
     return cudaGetLastError();
 }
 

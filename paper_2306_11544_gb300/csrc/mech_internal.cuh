@@ -200,12 +200,13 @@ cudaError_t launch_alive_flags(const uint8_t* alive, uint32_t n, uint32_t pad, u
 // flags[q] = (alive[st.id[q]] != 0) in state order, 0 up to pad.
 cudaError_t launch_keep_flags(const StepArgs& a, const StateBuf& st, const uint8_t* alive, uint32_t pad,
                               uint32_t* flags, cudaStream_t s);
-// Survivors of a.A move to a.B at dst[q] (exclusive prefix of the keep flags
-// over the state order) with caller index newid[id] (exclusive prefix of the
-// alive flags over the caller order); every state array is moved, whatever
-// the mode.
-cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
-                                 cudaStream_t s);
+// Survivors of a.A end in slots [0, n2) in place: the survivors at or above
+// n2 fill the dead slots below n2 (keep_pref: exclusive prefix of the keep
+// flags over the state order; hole: scratch of n2 entries), then every
+// survivor takes caller index newid[id] (exclusive prefix of the alive flags
+// over the caller order).  Every state array is moved, whatever the mode.
+cudaError_t launch_remove_in_place(const StepArgs& a, const uint8_t* alive, const uint32_t* keep_pref,
+                                   const uint32_t* newid, uint32_t n2, uint32_t* hole, cudaStream_t s);
 // FP64 parameters of the survivors (caller order) into io[0..np), io[np..2np),
 // io[2np..3np) at their new caller index.
 cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
