@@ -107,6 +107,22 @@ def reduce_max(x: float, pg, device) -> float:
     return float(t.item())
 
 
+def shard_replicates(counts, world: int):
+    """Replicates of an ensemble split over `world` ranks with no exchange
+    between them: largest first, each to the rank with the fewest cells so far
+    (ties to the lower rank).  Returns each rank's replicate indices in
+    ascending order."""
+    if world > len(counts):
+        raise ValueError(f"{world} ranks for {len(counts)} replicates")
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for r in sorted(range(len(counts)), key=lambda i: (-int(counts[i]), i)):
+        k = min(range(world), key=lambda w: (load[w], w))
+        out[k].append(r)
+        load[k] += int(counts[r])
+    return [sorted(x) for x in out]
+
+
 def job_throughput(cells_per_rank: int, world: int, steps: int, seconds: float) -> float:
     """Whole-job cell-steps/s: every rank advances its own replica by `steps`."""
     return cells_per_rank * world * steps / seconds
@@ -484,6 +500,16 @@ def main():
 
     wl = make_workload(args.workload, args.scale)
     batched = not isinstance(wl, synth.Population)
+    total_cells = None  # whole-job cells when the ranks share one ensemble
+    sharding = None
+    if batched and ws > 1:
+        # the ensemble's replicates are split over the ranks (strong scaling):
+        # each rank steps its own batch, with no data-path exchange
+        parts = shard_replicates([p.n for p in wl.reps], ws)
+        total_cells = wl.n_total
+        sharding = {"replicates_per_rank": [len(x) for x in parts],
+                    "cells_per_rank": [int(sum(wl.reps[i].n for i in x)) for x in parts]}
+        wl = synth.Ensemble(wl.name, [wl.reps[i] for i in parts[rank]], wl.steps, dict(wl.meta))
     if not batched:
         m = mech.Mech.from_population(wl, mode=args.mode)
         n = wl.n
@@ -543,8 +569,10 @@ def main():
     t_max = reduce_max(ms, pg, "cuda")
     if pg:
         pg.barrier()
-    total_cells = n * ws
-    value = job_throughput(n, ws, args.steps, t_max * 1e-3)
+    if total_cells is None:
+        value = job_throughput(n, ws, args.steps, t_max * 1e-3)
+    else:
+        value = total_cells * args.steps / (t_max * 1e-3)
     if not profile:  # graph run: phases from a short profiled pass after the timed region
         m.set_profiling(True)
         m.step(max(2, min(20, args.steps)))
@@ -555,7 +583,7 @@ def main():
     plain = None
     if batched and args.plain_loop:
         plain = time_plain_loop(wl, args, stream, torch)
-        plain["batched_over_plain"] = value / plain["value"]
+        plain["batched_over_plain"] = n * args.steps / (t_max * 1e-3) / plain["value"]  # this rank's replicates
 
     # end to end through the C ABI: pinned host positions in, step, positions out
     e2e = None
@@ -642,7 +670,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.mode], "data": "synthetic",
+        "scaling": "weak" if sharding is None else "strong", "vs_baseline": None, "dtype": DTYPES[args.mode],
+        "data": "synthetic",
         "config": describe(wl, args.workload, args, n, V),
         "roofline": roof,
         "step_roofline": {"bytes_per_step": step_bytes, "model": "228 B/cell + 20 B/voxel (workload voxel grid)",
@@ -656,6 +685,8 @@ def main():
     }
     if turnover is not None:
         line["turnover"] = turnover
+    if sharding is not None:
+        line["sharding"] = sharding
     if batched:
         line["batched"] = {"replicates": len(wl.reps), "graph_steps": args.graph,
                            "launches_per_step": info["launches_per_step"]}

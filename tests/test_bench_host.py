@@ -1,7 +1,10 @@
-"""Host logic of bench.py's turnover mode (no GPU): the precomputed death and
+"""Host logic of bench.py (no GPU): the turnover mode's precomputed death and
 division events keep the cell count, place each daughter half a radius from a
-survivor of that event, give it that cell's parameters, and are reproducible."""
+survivor of that event, give it that cell's parameters, and are
+reproducible; the ensemble's replicates are split over ranks once each and
+in balance."""
 import numpy as np
+import pytest
 
 import bench
 from paper_2306_11544_gb300 import synth
@@ -36,3 +39,17 @@ def test_turnover_events_keep_the_count_and_follow_survivors():
     for a, b in zip(events, again):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_replicate_sharding_covers_every_replicate_once_and_balances():
+    counts = [p.n for p in synth.ensemble_256(seed=0, scale=0.01).reps]
+    for world in (1, 2, 3, 8):
+        parts = bench.shard_replicates(counts, world)
+        flat = sorted(i for x in parts for i in x)
+        assert flat == list(range(len(counts)))  # each replicate on exactly one rank
+        loads = [sum(counts[i] for i in x) for x in parts]
+        # greedy largest-first: no rank exceeds the mean by more than the largest replicate
+        assert max(loads) - sum(counts) / world <= max(counts)
+        assert bench.shard_replicates(counts, world) == parts  # deterministic
+    with pytest.raises(ValueError):
+        bench.shard_replicates([5, 6], 3)
