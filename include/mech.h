@@ -199,35 +199,43 @@ MECH_API int mech_read_state(mech_t* h, double* xyz, double* vprev, double* comp
 MECH_API int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const double* comp, int64_t step);
 
 /*
- * Dynamic population (the cell count of a single-population handle changes
- * between steps, as cells divide and die).  Both calls are ordered after the
- * work already enqueued on the handle's stream and return when done; the
- * next step bins the new population (keys are recomputed from the
- * positions), and the handle's step count is unchanged.
+ * Dynamic population (the cell count changes between steps, as cells divide
+ * and die).  These calls are ordered after the work already enqueued on the
+ * handle's stream and return when done; the next step bins the new
+ * population (keys are recomputed from the positions), and the handle's step
+ * count is unchanged.  Every replicate of a batch stays one contiguous range
+ * of caller indices, in replicate order.
  *
- * mech_remove_cells: alive holds n bytes in caller order; the cells with
- * alive[i] == 0 are removed.  The survivors keep their relative order and are
- * renumbered 0 .. n'-1 (caller index i becomes the number of survivors
- * before it) with their whole state: position (and Kahan compensation),
- * previous velocity, radius and coefficients.  The device work is two prefix
- * sums, survivors moved into the dead cells' slots and a compaction of the
- * caller-order parameters; nothing changes when every cell is alive.
+ * mech_remove_cells: alive holds n bytes in caller order (all replicates);
+ * the cells with alive[i] == 0 are removed.  The survivors keep their
+ * relative order and are renumbered 0 .. n'-1 (caller index i becomes the
+ * number of survivors before it) with their whole state: position (and Kahan
+ * compensation), previous velocity, radius and coefficients.  The device work
+ * is two prefix sums and, for a single population, the survivors moved into
+ * the dead cells' slots (a batch: an order-preserving compaction), plus a
+ * compaction of the caller-order parameters; nothing changes when every cell
+ * is alive.
  *
- * mech_add_cells: appends m cells with caller indices n .. n+m-1, positions
- * xyz (3m doubles), radii, coefficients and types as in mech_create; their
- * previous velocity is zero (their AB2 starts as at creation).  When n + m
- * exceeds the device capacity, every per-cell buffer grows to max(n + m,
- * 1.5 n) cells (one copy of the state).  A radius for which the handle's
- * voxel (or internal voxel) is too small fails with MECH_E_VOXEL_TOO_SMALL
- * and non-finite or invalid cells with MECH_E_NONFINITE / MECH_E_ARG, before
- * anything changes.
+ * mech_add_cells (single population): appends m cells with caller indices
+ * n .. n+m-1, positions xyz (3m doubles), radii, coefficients and types as
+ * in mech_create; their previous velocity is zero (their AB2 starts as at
+ * creation).  mech_add_cells_batch: counts[r] new cells for replicate r
+ * (n_rep counts; the arrays hold them in replicate order); replicate r's new
+ * cells follow its existing ones and the later replicates' caller indices
+ * move up by the cells added before them.  When the total exceeds the device
+ * capacity, every per-cell buffer grows to max(n + m, 1.5 n) cells (one copy
+ * of the state).  A radius for which the handle's voxel (or internal voxel)
+ * is too small fails with MECH_E_VOXEL_TOO_SMALL and non-finite or invalid
+ * cells with MECH_E_NONFINITE / MECH_E_ARG, before anything changes.
  *
- * Both fail with MECH_E_ARG on batch handles (more than one replicate) and
+ * mech_add_cells on a batch handle fails with MECH_E_ARG; all three fail
  * with MECH_E_STATE on a handle a device error left inconsistent.
  */
 MECH_API int mech_remove_cells(mech_t* h, const uint8_t* alive);
 MECH_API int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr,
                             const double* cca, const int32_t* type);
+MECH_API int mech_add_cells_batch(mech_t* h, const int64_t* counts, const double* xyz, const double* R,
+                                  const double* ccr, const double* cca, const int32_t* type);
 
 /*
  * Binning of the current positions, for inspection (steps 1 of the update,

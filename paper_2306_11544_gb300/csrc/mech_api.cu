@@ -108,6 +108,8 @@ struct mech {
     uint32_t* d_cpref[2] = {nullptr, nullptr};
     uint32_t* d_cbsum = nullptr;
     size_t ccap = 0;
+    uint32_t* d_shift = nullptr;  // mech_add_cells_batch: per-replicate shift
+    size_t shift_cap = 0;
     float* d_vout_f = nullptr;
     double* d_vout_d = nullptr;
     bool vout_valid = false;
@@ -595,14 +597,32 @@ int grow_capacity(mech_t* h, size_t cap2) {
     return MECH_OK;
 }
 
-// Bookkeeping after the cell count changed.
-void set_cell_count(mech_t* h, int64_t n) {
-    h->n = n;
-    h->counts[0] = n;
-    h->elem_grid = (int)std::min<int64_t>(std::max<int64_t>(h->sms * 8, (n + 1023) / 1024), 1 << 20);
+// Bookkeeping after the cell counts changed: per-replicate counts and first
+// cells, the grid descriptors' cell ranges (the device copy too, when the
+// grids are built), launch sizes; keys, velocities-only output and graphs
+// are invalid.
+int set_cell_counts(mech_t* h, const std::vector<int64_t>& counts) {
+    h->counts = counts;
+    int64_t run = 0;
+    for (int r = 0; r < h->nrep; ++r) {
+        h->cbase[r] = run;
+        run += counts[r];
+    }
+    h->n = run;
+    h->elem_grid = (int)std::min<int64_t>(std::max<int64_t>(h->sms * 8, (run + 1023) / 1024), 1 << 20);
     h->keys_valid = false;
     h->vout_valid = false;
     h->invalidate_graphs();
+    if (!h->grid_dirty && (int)h->grids.size() == h->nrep && h->d_grids) {
+        for (int r = 0; r < h->nrep; ++r) {
+            h->grids[r].cbase = (uint32_t)h->cbase[r];
+            h->grids[r].ncell = (uint32_t)h->counts[r];
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->d_grids, h->grids.data(), h->grids.size() * sizeof(GridDev),
+                                 cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host copy may change again
+    }
+    return MECH_OK;
 }
 
 int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double* xyz, const double* R,
@@ -1034,12 +1054,18 @@ int mech_load_state(mech_t* h, const double* xyz, const double* vprev, const dou
 
 int mech_remove_cells(mech_t* h, const uint8_t* alive) {
     MECH_TRY(check_handle(h));
-    if (h->nrep != 1) return fail(MECH_E_ARG, "mech_remove_cells: single-population handles only");
     if (h->poisoned)
         return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
     const uint32_t n = (uint32_t)h->n;
     if (n == 0) return MECH_OK;
     if (!alive) return fail(MECH_E_ARG, "null alive mask");
+    // survivors per replicate (caller ranges), from the host mask
+    std::vector<int64_t> counts2(h->nrep, 0);
+    for (int r = 0; r < h->nrep; ++r)
+        for (int64_t i = h->cbase[r]; i < h->cbase[r] + h->counts[r]; ++i) counts2[r] += alive[i] != 0;
+    int64_t n2 = 0;
+    for (int64_t c : counts2) n2 += c;
+    if (n2 == (int64_t)n) return MECH_OK;
     // scratch for the two prefix sums (padded to the scan's tile)
     const size_t need = ((size_t)h->npad + kScanTile - 1) / kScanTile * kScanTile;
     if (h->ccap < need) {
@@ -1063,22 +1089,24 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
     const uint32_t pad = (uint32_t)(((size_t)n + kScanTile - 1) / kScanTile * kScanTile);
     StepArgs a = h->args(h->cur, 1);
     uint32_t* newid = h->d_cpref[0];
-    uint32_t* dst = h->d_cpref[1];
+    uint32_t* keep_pref = h->d_cpref[1];
     // new caller index of each survivor: exclusive prefix of the alive flags
     CUDA_TRY(cudaMemcpyAsync(h->d_alive, alive, n, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(launch_alive_flags(h->d_alive, n, pad, h->d_cflags, h->stream));
     CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, newid, nullptr, nullptr, h->stream));
-    uint32_t last[2] = {0, 0};
-    CUDA_TRY(cudaMemcpyAsync(&last[0], newid + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(&last[1], h->d_cflags + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    const uint32_t n2 = last[0] + last[1];
-    if (n2 == n) return MECH_OK;
-    // survivors into slots [0, n2) in place: the keep flags' exclusive prefix
-    // in state order numbers the holes below n2 and the movers above it
+    // exclusive prefix of the keep flags in state order
     CUDA_TRY(launch_keep_flags(a, h->st[h->cur], h->d_alive, pad, h->d_cflags, h->stream));
-    CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, dst, nullptr, nullptr, h->stream));
-    CUDA_TRY(launch_remove_in_place(a, h->d_alive, dst, newid, n2, h->d_cflags, h->stream));
+    CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, keep_pref, nullptr, nullptr, h->stream));
+    if (h->nrep == 1) {
+        // one population: the survivors at or above n2 fill the dead slots below
+        // it, in place (only as many cells move as died below n2)
+        CUDA_TRY(launch_remove_in_place(a, h->d_alive, keep_pref, newid, (uint32_t)n2, h->d_cflags, h->stream));
+    } else {
+        // a batch: order-preserving compaction into the other state buffer, so
+        // that every replicate stays one contiguous range
+        CUDA_TRY(launch_compact_state(a, h->d_alive, keep_pref, newid, h->stream));
+        h->cur ^= 1;
+    }
     CUDA_TRY(launch_compact_params(a, h->d_alive, newid, h->d_io, h->stream));
     const size_t np = h->npad;
     if (n2 > 0) {
@@ -1086,18 +1114,30 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
         CUDA_TRY(cudaMemcpyAsync(h->d_ccr64, h->d_io + np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
         CUDA_TRY(cudaMemcpyAsync(h->d_cca64, h->d_io + 2 * np, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
     }
-    set_cell_count(h, n2);
+    MECH_TRY(set_cell_counts(h, counts2));
     return mech_sync(h);
 }
 
-int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr, const double* cca,
-                   const int32_t* type) {
-    (void)type;
+// New cells: per_rep[r] of them for replicate r (all of them for a single
+// population), given in replicate order.
+static int add_cells(mech_t* h, const int64_t* per_rep, int64_t m, const double* xyz, const double* R,
+                     const double* ccr, const double* cca) {
     MECH_TRY(check_handle(h));
-    if (h->nrep != 1) return fail(MECH_E_ARG, "mech_add_cells: single-population handles only");
     if (h->poisoned)
         return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
     if (m < 0) return fail(MECH_E_ARG, "negative cell count");
+    std::vector<int64_t> add(h->nrep, 0);
+    if (per_rep) {
+        int64_t s = 0;
+        for (int r = 0; r < h->nrep; ++r) {
+            if (per_rep[r] < 0) return fail(MECH_E_ARG, "negative cell count for a replicate");
+            add[r] = per_rep[r];
+            s += per_rep[r];
+        }
+        if (s != m) return fail(MECH_E_ARG, "per-replicate counts do not add up to m");
+    } else {
+        add[0] = m;
+    }
     if (m == 0) return MECH_OK;
     MECH_TRY(validate_cells(m, xyz, R, ccr, cca));
     if (h->n + m >= (int64_t)0x7FFFFFFF) return fail(MECH_E_ARG, "more than 2^31-1 cells");
@@ -1115,18 +1155,71 @@ int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, con
         const size_t cap2 = (size_t)(std::max<int64_t>(n + m, n + n / 2) + 63) / 64 * 64;
         MECH_TRY(grow_capacity(h, cap2));
     }
-    // parameters and positions; the kernel writes the records, ids and state
-    const StateBuf& s = h->st[h->cur];
     cudaStream_t st = h->stream;
-    CUDA_TRY(cudaMemcpyAsync(h->d_R64 + n, R, m * 8, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(h->d_ccr64 + n, ccr, m * 8, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(h->d_cca64 + n, cca, m * 8, cudaMemcpyHostToDevice, st));
+    const size_t np = h->npad;
+    // replicate r's cells move up by the cells added before it
+    std::vector<uint32_t> shift(h->nrep, 0);
+    bool shifted = false;
+    for (int r = 1; r < h->nrep; ++r) {
+        shift[r] = shift[r - 1] + (uint32_t)add[r - 1];
+        shifted = shifted || (shift[r] > 0 && h->counts[r] > 0);
+    }
+    if (shifted) {
+        if (h->shift_cap < (size_t)h->nrep) {
+            h->free_ptr(h->d_shift, h->shift_cap * 4);
+            h->d_shift = nullptr;
+            h->shift_cap = 0;
+            MECH_TRY(h->alloc(&h->d_shift, (size_t)h->nrep));
+            h->shift_cap = (size_t)h->nrep;
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->d_shift, shift.data(), h->nrep * 4, cudaMemcpyHostToDevice, st));
+        StepArgs a = h->args(h->cur, 1);
+        CUDA_TRY(launch_shift(a, h->d_shift, h->d_io, st));
+        h->cur ^= 1;
+        CUDA_TRY(cudaMemcpyAsync(h->d_R64, h->d_io, (n + m) * 8, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(h->d_ccr64, h->d_io + np, (n + m) * 8, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(h->d_cca64, h->d_io + 2 * np, (n + m) * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    // slot (= caller index) of every new cell: after its replicate's cells
+    std::vector<uint32_t> dst(m);
+    std::vector<int64_t> counts2(h->nrep);
+    int64_t k = 0, base = 0;
+    for (int r = 0; r < h->nrep; ++r) {
+        for (int64_t j = 0; j < add[r]; ++j) dst[k++] = (uint32_t)(base + h->counts[r] + j);
+        counts2[r] = h->counts[r] + add[r];
+        base += counts2[r];
+    }
+    // new cells' positions and parameters, packed in io; dst in perm (binning
+    // scratch, free between steps)
     CUDA_TRY(cudaMemcpyAsync(h->d_io, xyz, 3 * m * 8, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(launch_append_state(h->args(h->cur, 1), s, h->d_io, (uint32_t)n, (uint32_t)m, st));
-    CUDA_TRY(cudaStreamSynchronize(st));  // the caller's arrays may be released on return
+    CUDA_TRY(cudaMemcpyAsync(h->d_io + 3 * m, R, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_io + 4 * m, ccr, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_io + 5 * m, cca, m * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->d_perm, dst.data(), m * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_append_state(h->args(h->cur, 1), h->st[h->cur], h->d_io, h->d_perm, (uint32_t)m, h->d_R64,
+                                 h->d_ccr64, h->d_cca64, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above and the caller's arrays are released
     h->maxR = maxR;
-    set_cell_count(h, n + m);
+    MECH_TRY(set_cell_counts(h, counts2));
     return mech_sync(h);
+}
+
+int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr, const double* cca,
+                   const int32_t* type) {
+    (void)type;
+    MECH_TRY(check_handle(h));
+    if (h->nrep != 1) return fail(MECH_E_ARG, "mech_add_cells: use mech_add_cells_batch for a batch handle");
+    return add_cells(h, nullptr, m, xyz, R, ccr, cca);
+}
+
+int mech_add_cells_batch(mech_t* h, const int64_t* counts, const double* xyz, const double* R, const double* ccr,
+                         const double* cca, const int32_t* type) {
+    (void)type;
+    MECH_TRY(check_handle(h));
+    if (!counts) return fail(MECH_E_ARG, "null counts");
+    int64_t m = 0;
+    for (int r = 0; r < h->nrep; ++r) m += counts[r];
+    return add_cells(h, counts, m, xyz, R, ccr, cca);
 }
 
 int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order) {

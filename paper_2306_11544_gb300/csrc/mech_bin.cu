@@ -406,16 +406,90 @@ __global__ void k_compact_params(const StepArgs a, const uint8_t* __restrict__ a
     }
 }
 
-__global__ void k_append_state(const StepArgs a, const StateBuf st, const double* __restrict__ io, uint32_t n0,
-                               uint32_t m) {
+// Order-preserving removal for batches: survivors of a.A go to a.B at dst[q]
+// (exclusive prefix of the keep flags over the state order), so every
+// replicate's cells stay one contiguous range; caller index newid[id].
+__global__ void k_compact_state(const StepArgs a, const uint8_t* __restrict__ alive, const uint32_t* __restrict__ dst,
+                                const uint32_t* __restrict__ newid) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t id = a.A.id[q];
+        if (id >= a.n) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        if (!alive[id]) continue;
+        const uint32_t f = dst[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            a.B.pos64[d * np + f] = a.A.pos64[d * np + q];
+            a.B.posf[d * np + f] = a.A.posf[d * np + q];
+            a.B.comp[d * np + f] = a.A.comp[d * np + q];
+            a.B.vp64[d * np + f] = a.A.vp64[d * np + q];
+            a.B.vpf[d * np + f] = a.A.vpf[d * np + q];
+        }
+        a.B.rec[2 * (size_t)f] = a.A.rec[2 * (size_t)q];
+        a.B.rec[2 * (size_t)f + 1] = a.A.rec[2 * (size_t)q + 1];
+        a.B.id[f] = newid[id];
+    }
+}
+
+// Additions to a batch: every cell of replicate r moves up by shift[r] (the
+// cells added to the replicates before r), in state order (A -> B) and in
+// caller order (its id and, into io, its FP64 parameters).
+__global__ void k_shift_state(const StepArgs a, const uint32_t* __restrict__ shift) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t s = shift[rep_of_cell(a.grids, a.nrep, q)];
+        const size_t f = (size_t)q + s;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            a.B.pos64[d * np + f] = a.A.pos64[d * np + q];
+            a.B.posf[d * np + f] = a.A.posf[d * np + q];
+            a.B.comp[d * np + f] = a.A.comp[d * np + q];
+            a.B.vp64[d * np + f] = a.A.vp64[d * np + q];
+            a.B.vpf[d * np + f] = a.A.vpf[d * np + q];
+        }
+        a.B.rec[2 * f] = a.A.rec[2 * (size_t)q];
+        a.B.rec[2 * f + 1] = a.A.rec[2 * (size_t)q + 1];
+        a.B.id[f] = a.A.id[q] + s;  // a replicate's caller indices and slots span the same range
+    }
+}
+
+__global__ void k_shift_params(const StepArgs a, const uint32_t* __restrict__ shift, double* __restrict__ io) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const size_t j = (size_t)i + shift[rep_of_cell(a.grids, a.nrep, i)];
+        io[j] = a.R64[i];
+        io[np + j] = a.ccr64[i];
+        io[2 * np + j] = a.cca64[i];
+    }
+}
+
+// New cell k goes to slot and caller index dst[k]; io holds the m new
+// positions (3 per cell) at io[0, 3m) and their R, ccr, cca at io[3m + k],
+// io[4m + k], io[5m + k].
+__global__ void k_append_state(const StepArgs a, const StateBuf st, const double* __restrict__ io,
+                               const uint32_t* __restrict__ dst, uint32_t m, double* __restrict__ R64,
+                               double* __restrict__ ccr64, double* __restrict__ cca64) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const size_t np = a.npad;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const size_t q = (size_t)n0 + j;
+        const size_t q = dst[j];
+        if (q >= np) {  // the host computed every dst below the capacity
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        const double R = io[3 * (size_t)m + j], ccr = io[4 * (size_t)m + j], cca = io[5 * (size_t)m + j];
+        R64[q] = R;
+        ccr64[q] = ccr;
+        cca64[q] = cca;
         // record: radius as FP32 plus its residual in units of ulp(R) / 2^15
         // (16 bits, offset 2^15), coefficient square roots; the position
         // fields are written by the next canonicalisation
-        const double R = a.R64[q];
         const float Rf = __double2float_rn(R);
         int e2 = 0;
         frexpf(Rf, &e2);  // Rf = f 2^e2, f in [0.5, 1): ulp(Rf) = 2^(e2 - 24)
@@ -423,9 +497,9 @@ __global__ void k_append_state(const StepArgs a, const StateBuf st, const double
         const long long L = llround(fmin(32767.0, fmax(-32768.0, units * 32768.0)));
         const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
         st.rec[2 * q] = make_float4(0.f, 0.f, 0.f, Rf);
-        st.rec[2 * q + 1] = make_float4(__double2float_rn(sqrt(a.ccr64[q])), __double2float_rn(sqrt(a.cca64[q])),
+        st.rec[2 * q + 1] = make_float4(__double2float_rn(sqrt(ccr)), __double2float_rn(sqrt(cca)),
                                         __uint_as_float(0x80008000u), __uint_as_float(wzr));
-        st.id[q] = (uint32_t)q;  // caller order: appended cells take indices n0 .. n0+m-1
+        st.id[q] = (uint32_t)q;  // a new cell's caller index is its slot
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double x = io[3 * (size_t)j + d];
@@ -525,10 +599,24 @@ cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, uint32_t n0, uint32_t m,
-                                cudaStream_t s) {
+cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, const uint32_t* dst,
+                                uint32_t m, double* R64, double* ccr64, double* cca64, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
-    k_append_state<<<elementwise_grid(m), 256, 0, s>>>(a, st, io, n0, m);
+    k_append_state<<<elementwise_grid(m), 256, 0, s>>>(a, st, io, dst, m, R64, ccr64, cca64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
+                                 cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_compact_state<<<elementwise_grid(a.n), 256, 0, s>>>(a, alive, dst, newid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const StepArgs& a, const uint32_t* shift, double* io, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_shift_state<<<elementwise_grid(a.n), 256, 0, s>>>(a, shift);
+    k_shift_params<<<elementwise_grid(a.n), 256, 0, s>>>(a, shift, io);
     return cudaGetLastError();
 }
 

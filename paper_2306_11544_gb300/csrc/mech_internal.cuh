@@ -211,12 +211,19 @@ cudaError_t launch_remove_in_place(const StepArgs& a, const uint8_t* alive, cons
 // io[2np..3np) at their new caller index.
 cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
                                   cudaStream_t s);
-// Cells n0 .. n0+m-1 of st (caller indices n0 .. n0+m-1): positions from io
-// (3 doubles per cell, rounded as by mech_write_positions), zero previous
-// velocity, force records from the FP64 parameters a.R64/ccr64/cca64 (already
-// in place at n0 .. n0+m-1).
-cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, uint32_t n0, uint32_t m,
-                                cudaStream_t s);
+// New cell k of m goes to slot and caller index dst[k] of st: FP64
+// parameters (into R64, ccr64, cca64, caller order), force record, position
+// (rounded as by mech_write_positions) and zero previous velocity, from io
+// (positions at [0, 3m), R, ccr, cca at [3m, 4m), [4m, 5m), [5m, 6m)).
+cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, const uint32_t* dst,
+                                uint32_t m, double* R64, double* ccr64, double* cca64, cudaStream_t s);
+// Batches: order-preserving removal from a.A into a.B (dst: exclusive prefix
+// of the keep flags over the state order), every replicate staying one range.
+cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
+                                 cudaStream_t s);
+// Batches: every cell of replicate r moves up by shift[r], state A -> B and
+// its FP64 parameters into io[0..np), io[np..2np), io[2np..3np).
+cudaError_t launch_shift(const StepArgs& a, const uint32_t* shift, double* io, cudaStream_t s);
 cudaError_t launch_unpermute_vel(const StepArgs& a, const StateBuf& st, const float* vf, const double* vd,
                                  double* out, cudaStream_t s);
 cudaError_t launch_load_pos(const StepArgs& a, const StateBuf& st, const double* in, int raw_kahan,

@@ -43,7 +43,8 @@ EXPORTS = [
     "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
-    "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_debug_bins", "mech_pair_stats", "mech_bin_noalloc",
+    "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_add_cells_batch", "mech_debug_bins",
+    "mech_pair_stats", "mech_bin_noalloc",
     "mech_debug_inject", "mech_info", "mech_grid", "mech_destroy",
 ]
 
@@ -109,6 +110,7 @@ def load_library(path: str = LIB_PATH):
             "mech_load_state": ([_P, _P, _P, _P, ctypes.c_int64], ctypes.c_int),
             "mech_remove_cells": ([_P, _P], ctypes.c_int),
             "mech_add_cells": ([_P, ctypes.c_int64, _P, _P, _P, _P, _P], ctypes.c_int),
+            "mech_add_cells_batch": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
             "mech_debug_bins": ([_P, _P, _P, _P, _P], ctypes.c_int),
             "mech_pair_stats": ([_P, _P, _P], ctypes.c_int),
             "mech_bin_noalloc": ([ctypes.c_int64, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -177,16 +179,24 @@ def mech_remove_cells(h, n, alive):
     return int(np.count_nonzero(a))
 
 
-def mech_add_cells(h, xyz, R, ccr, cca, ctype=None):
-    """Append cells (caller indices n .. n+m-1); returns m."""
+def mech_add_cells(h, xyz, R, ccr, cca, ctype=None, counts=None):
+    """Append cells; returns m.  counts (batch handles): new cells per
+    replicate, the arrays holding them in replicate order."""
     xyz = _f64(xyz).reshape(-1)
     m = xyz.size // 3
     if xyz.size != 3 * m:
         raise ValueError("xyz must hold 3 values per cell")
     R, ccr, cca = _f64(R, m), _f64(ccr, m), _f64(cca, m)
     t = None if ctype is None else np.ascontiguousarray(ctype, dtype=np.int32)
-    _check(load_library().mech_add_cells(h, int(m), _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), _ptr(t)),
-           "mech_add_cells")
+    if counts is None:
+        _check(load_library().mech_add_cells(h, int(m), _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), _ptr(t)),
+               "mech_add_cells")
+    else:
+        c = np.ascontiguousarray(counts, dtype=np.int64)
+        if int(c.sum()) != m:  # the library reads sum(counts) cells from the arrays
+            raise ValueError(f"counts add up to {int(c.sum())}, the arrays hold {m} cells")
+        _check(load_library().mech_add_cells_batch(h, _ptr(c), _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), _ptr(t)),
+               "mech_add_cells_batch")
     return m
 
 
@@ -455,13 +465,17 @@ class Mech:
 
     def remove_cells(self, alive):
         """Keep the cells whose flag is true; survivors are renumbered in order."""
+        alive = np.asarray(alive).reshape(-1)
         self.n = mech_remove_cells(self.h, self.n, alive)
-        self.counts = np.array([self.n], dtype=np.int64)
+        edges = np.concatenate([[0], np.cumsum(self.counts)])
+        self.counts = np.array([np.count_nonzero(alive[a:b]) for a, b in zip(edges[:-1], edges[1:])], dtype=np.int64)
 
-    def add_cells(self, xyz, R, ccr, cca, ctype=None):
-        """Append cells after the current ones (zero previous velocity)."""
-        self.n += mech_add_cells(self.h, xyz, R, ccr, cca, ctype)
-        self.counts = np.array([self.n], dtype=np.int64)
+    def add_cells(self, xyz, R, ccr, cca, ctype=None, counts=None):
+        """Append cells after the current ones (zero previous velocity); a
+        batch takes counts, the new cells per replicate in replicate order."""
+        self.n += mech_add_cells(self.h, xyz, R, ccr, cca, ctype, counts)
+        self.counts = (np.array([self.n], dtype=np.int64) if counts is None
+                       else self.counts + np.asarray(counts, dtype=np.int64))
 
     def bins(self):
         return mech_debug_bins(self.h, self.n)

@@ -197,9 +197,59 @@ def test_invalid_changes_are_refused_before_anything_changes():
         assert np.array_equal(before[k], after[k]), k
     ens = synth.ensemble_256(seed=32, scale=0.01, n_rep=3)
     with mech.Mech.from_ensemble(ens, mode="mixed") as b:
-        with pytest.raises(mech.MechError) as e:
-            b.remove_cells(np.ones(b.n, bool))
-        assert e.value.code == mech.MECH_E_ARG
-        with pytest.raises(mech.MechError) as e:
+        with pytest.raises(mech.MechError) as e:  # a batch needs the per-replicate counts
             b.add_cells([[0.0, 0.0, 0.0]], [8.0], [10.0], [0.4])
         assert e.value.code == mech.MECH_E_ARG
+        with pytest.raises(ValueError):
+            b.add_cells([[0.0, 0.0, 0.0]], [8.0], [10.0], [0.4], counts=[1, 1, 0])
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "kahan"])
+def test_batch_turnover_equals_separate_handles(mode):
+    """Four replicates in one batch (one of them emptied, one growing from
+    nothing) and four separate handles take the same deaths and divisions:
+    the batch gives, replicate by replicate, exactly the separate handles'
+    positions and velocities (every replicate stays one range of caller
+    indices)."""
+    ens = synth.ensemble_256(seed=33, scale=0.02, n_rep=4)
+    rng = np.random.Generator(np.random.PCG64(34))
+    reps = ens.reps
+    with mech.Mech.from_ensemble(ens, mode=mode) as b:
+        singles = [H.make(p, mode) for p in reps]
+        try:
+            for event in range(2):
+                b.step(4)
+                for s in singles:
+                    s.step(4)
+                xs = [s.positions() for s in singles]
+                masks = [rng.random(s.n) >= 0.1 for s in singles]
+                if event == 0:
+                    masks[1][:] = False  # replicate 1 dies out
+                add = [int(rng.integers(0, 30)) for _ in singles]
+                if event == 1:
+                    add[1] = 25  # and grows again
+                new = []
+                for r, (s, mk, k) in enumerate(zip(singles, masks, add)):
+                    src = xs[r][mk] if mk.any() else reps[r].xyz
+                    j = rng.integers(0, len(src), size=k)
+                    xyz = src[j] + rng.normal(0, 2.0, size=(k, 3))
+                    new.append((xyz, np.full(k, reps[r].R.max()), np.full(k, reps[r].ccr[0]),
+                                np.full(k, reps[r].cca[0])))
+                b.remove_cells(np.concatenate(masks))
+                b.add_cells(*(np.concatenate([x[f] for x in new]) for f in range(4)), counts=add)
+                for s, mk, (xyz, R, ccr, cca) in zip(singles, masks, new):
+                    s.remove_cells(mk)
+                    s.add_cells(xyz, R, ccr, cca)
+                assert list(b.counts) == [s.n for s in singles]
+            b.step(5)
+            xb, vb = b.positions(), b.velocities()
+            off = 0
+            for r, s in enumerate(singles):
+                s.step(5)
+                x, v = s.positions(), s.velocities()
+                assert np.array_equal(xb[off:off + s.n], x), r
+                assert np.array_equal(vb[off:off + s.n], v), r
+                off += s.n
+        finally:
+            for s in singles:
+                s.close()
