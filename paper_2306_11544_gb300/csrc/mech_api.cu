@@ -1059,13 +1059,16 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
     const uint32_t n = (uint32_t)h->n;
     if (n == 0) return MECH_OK;
     if (!alive) return fail(MECH_E_ARG, "null alive mask");
-    // survivors per replicate (caller ranges), from the host mask
+    // survivors per replicate (caller ranges): of a batch from the host mask;
+    // of a single population from the device prefix sum below
     std::vector<int64_t> counts2(h->nrep, 0);
-    for (int r = 0; r < h->nrep; ++r)
-        for (int64_t i = h->cbase[r]; i < h->cbase[r] + h->counts[r]; ++i) counts2[r] += alive[i] != 0;
     int64_t n2 = 0;
-    for (int64_t c : counts2) n2 += c;
-    if (n2 == (int64_t)n) return MECH_OK;
+    if (h->nrep > 1) {
+        for (int r = 0; r < h->nrep; ++r)
+            for (int64_t i = h->cbase[r]; i < h->cbase[r] + h->counts[r]; ++i) counts2[r] += alive[i] != 0;
+        for (int64_t c : counts2) n2 += c;
+        if (n2 == (int64_t)n) return MECH_OK;
+    }
     // scratch for the two prefix sums (padded to the scan's tile)
     const size_t need = ((size_t)h->npad + kScanTile - 1) / kScanTile * kScanTile;
     if (h->ccap < need) {
@@ -1094,6 +1097,15 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
     CUDA_TRY(cudaMemcpyAsync(h->d_alive, alive, n, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(launch_alive_flags(h->d_alive, n, pad, h->d_cflags, h->stream));
     CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, newid, nullptr, nullptr, h->stream));
+    if (h->nrep == 1) {
+        uint32_t last[2] = {0, 0};
+        CUDA_TRY(cudaMemcpyAsync(&last[0], newid + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(&last[1], h->d_cflags + (n - 1), 4, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        n2 = (int64_t)last[0] + last[1];
+        counts2[0] = n2;
+        if (n2 == (int64_t)n) return MECH_OK;
+    }
     // exclusive prefix of the keep flags in state order
     CUDA_TRY(launch_keep_flags(a, h->st[h->cur], h->d_alive, pad, h->d_cflags, h->stream));
     CUDA_TRY(launch_scan(h->d_cflags, pad, h->d_cbsum, keep_pref, nullptr, nullptr, h->stream));

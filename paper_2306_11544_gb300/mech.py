@@ -176,7 +176,7 @@ def mech_remove_cells(h, n, alive):
     if a.size != n:
         raise ValueError(f"expected {n} flags, got {a.size}")
     _check(load_library().mech_remove_cells(h, _ptr(a)), "mech_remove_cells")
-    return int(np.count_nonzero(a))
+    return int(mech_info(h)["n_cells"])
 
 
 def mech_add_cells(h, xyz, R, ccr, cca, ctype=None, counts=None):
@@ -467,8 +467,12 @@ class Mech:
         """Keep the cells whose flag is true; survivors are renumbered in order."""
         alive = np.asarray(alive).reshape(-1)
         self.n = mech_remove_cells(self.h, self.n, alive)
-        edges = np.concatenate([[0], np.cumsum(self.counts)])
-        self.counts = np.array([np.count_nonzero(alive[a:b]) for a, b in zip(edges[:-1], edges[1:])], dtype=np.int64)
+        if len(self.counts) == 1:
+            self.counts = np.array([self.n], dtype=np.int64)
+        else:  # survivors per replicate
+            edges = np.concatenate([[0], np.cumsum(self.counts)])
+            self.counts = np.array([np.count_nonzero(alive[a:b]) for a, b in zip(edges[:-1], edges[1:])],
+                                   dtype=np.int64)
 
     def add_cells(self, xyz, R, ccr, cca, ctype=None, counts=None):
         """Append cells after the current ones (zero previous velocity); a
