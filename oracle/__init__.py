@@ -1,4 +1,5 @@
-"""Oracle for the cell-mechanics step: plain FP64 CPU code (``mech_oracle.c``).
+"""Oracles: plain FP64 CPU code for the cell-mechanics step (``mech_oracle.c``)
+and for the substrate diffusion step and its gradients (``diffusion_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -7,8 +8,10 @@ shares no code with it.
 
 The C file holds the definition (binning by stable counting sort, the
 neighbour-gather repulsion/adhesion velocity of the paper's "update velocity"
-region, Sec. 5.4, and two-step Adams-Bashforth integration).  This module only
-compiles it and marshals numpy arrays; it adds no arithmetic of its own.
+region, Sec. 5.4, and two-step Adams-Bashforth integration); the second the
+diffusion-decay step (three one-dimensional implicit solves, no-flux faces)
+and the gradients of the microenvironment regions of Sec. 5.1-5.2.  This module
+only compiles them and marshals numpy arrays; it adds no arithmetic of its own.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mech_oracle.c")
+_SRC_DIFF = os.path.join(_HERE, "diffusion_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,12 +33,13 @@ CFLAGS = ["-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 
 def build_command():
-    return ["gcc", *CFLAGS, _SRC, "-o", _LIB, "-lm"]
+    return ["gcc", *CFLAGS, _SRC, _SRC_DIFF, "-o", _LIB, "-lm"]
 
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to its source (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                                                          os.path.getmtime(_SRC_DIFF)):
         subprocess.run(build_command(), check=True)
     return _LIB
 
@@ -83,6 +88,10 @@ class OracleLib:
         lib.oracle_ab2.argtypes = [_I64, _P, _P, _P, _D]
         lib.oracle_run.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _I64, _P]
         lib.oracle_run.restype = ctypes.c_int
+        if hasattr(lib, "oracle_diffusion_step"):  # absent from single-file test variants
+            lib.oracle_diffusion_step.argtypes = [_I64, _I64, _I64, ctypes.c_int32, _P, _P, _P, _D, _D, _I64]
+            lib.oracle_diffusion_step.restype = ctypes.c_int
+            lib.oracle_diffusion_gradient.argtypes = [_I64, _I64, _I64, ctypes.c_int32, _P, _D, _P]
         self.lib = lib
         self.path = path
 
@@ -201,6 +210,25 @@ class OracleLib:
         return xyz, vprev, v
 
 
+    def diffusion_step(self, rho, D, lam, dx, dt, steps):
+        """rho: (S, nz, ny, nx) densities, advanced `steps` steps (a copy is returned)."""
+        rho = _f64(rho).copy()
+        S, nz, ny, nx = rho.shape
+        D, lam = _f64(D, S), _f64(lam, S)
+        if self.lib.oracle_diffusion_step(nx, ny, nz, S, _ptr(rho), _ptr(D), _ptr(lam), float(dx), float(dt),
+                                          int(steps)) != 0:
+            raise MemoryError("oracle_diffusion_step: allocation failed")
+        return rho
+
+    def diffusion_gradient(self, rho, dx):
+        """Gradients (S, 3, nz, ny, nx) of rho (S, nz, ny, nx)."""
+        rho = _f64(rho)
+        S, nz, ny, nx = rho.shape
+        out = np.empty((S, 3, nz, ny, nx))
+        self.lib.oracle_diffusion_gradient(nx, ny, nz, S, _ptr(rho), float(dx), _ptr(out))
+        return out
+
+
 def _load() -> OracleLib:
     global _lib
     with _lock:
@@ -269,6 +297,14 @@ def ab2(xyz, v, vprev, dt):
 
 def run(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, vprev=None):
     return _load().run(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, vprev)
+
+
+def diffusion_step(rho, D, lam, dx, dt, steps):
+    return _load().diffusion_step(rho, D, lam, dx, dt, steps)
+
+
+def diffusion_gradient(rho, dx):
+    return _load().diffusion_gradient(rho, dx)
 
 
 def grid_dims(lo, hi, h):
