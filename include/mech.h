@@ -328,6 +328,33 @@ MECH_API int mech_grid(mech_t* h, int32_t rep, double* lo3, int32_t* dims3, int6
 /* Release every device and host resource of the handle (NULL is a no-op). */
 MECH_API int mech_destroy(mech_t* h);
 
+/*
+ * Substrate diffusion (the microenvironment solver and gradient regions of
+ * Sec. 5.1-5.2, run on a 75^3-voxel domain in the paper).  S densities on
+ * nx x ny x nz cubic voxels of side dx, array [s][z][y][x] (FP64), diffusion
+ * coefficients D[s] and decay rates lambda[s] (both >= 0), no flux through
+ * the faces.  mech_diffusion_step advances n_steps steps of length dt, each
+ * three one-dimensional backward-Euler solves (x, then y, then z) with the
+ * decay split equally among them, solved by the Thomas algorithm in FP64
+ * with IEEE operations in a fixed order (the results are reproducible bit for
+ * bit); asynchronous on the handle's stream.  mech_diffusion_gradient
+ * computes the gradients (central differences inside, one-sided at the
+ * faces; array [s][axis][z][y][x]) and copies them out when grad is not
+ * NULL; synchronous.  Densities start at zero; write/read copy all S fields
+ * (synchronous).
+ */
+typedef struct mech_diffusion mech_diffusion_t;
+
+MECH_API int mech_diffusion_create(mech_diffusion_t** out, int64_t nx, int64_t ny, int64_t nz, int32_t n_substrates,
+                                   double dx, const double* D, const double* lambda);
+MECH_API int mech_diffusion_destroy(mech_diffusion_t* h);
+MECH_API int mech_diffusion_set_stream(mech_diffusion_t* h, void* stream);
+MECH_API int mech_diffusion_write(mech_diffusion_t* h, const double* rho);
+MECH_API int mech_diffusion_read(mech_diffusion_t* h, double* rho);
+MECH_API int mech_diffusion_step(mech_diffusion_t* h, double dt, int64_t n_steps);
+MECH_API int mech_diffusion_gradient(mech_diffusion_t* h, double* grad);
+MECH_API int mech_diffusion_sync(mech_diffusion_t* h);
+
 #ifdef __cplusplus
 }
 #endif

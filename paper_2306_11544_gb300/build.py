@@ -12,7 +12,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmech.so")
-SOURCES = ["mech_api.cu", "mech_bin.cu", "mech_force.cu", "mech_noalloc.cu"]
+SOURCES = ["mech_api.cu", "mech_bin.cu", "mech_force.cu", "mech_noalloc.cu", "diffusion.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

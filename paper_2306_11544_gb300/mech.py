@@ -46,6 +46,8 @@ EXPORTS = [
     "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_add_cells_batch", "mech_debug_bins",
     "mech_pair_stats", "mech_bin_noalloc",
     "mech_debug_inject", "mech_info", "mech_grid", "mech_destroy",
+    "mech_diffusion_create", "mech_diffusion_destroy", "mech_diffusion_set_stream", "mech_diffusion_write",
+    "mech_diffusion_read", "mech_diffusion_step", "mech_diffusion_gradient", "mech_diffusion_sync",
 ]
 
 
@@ -118,6 +120,15 @@ def load_library(path: str = LIB_PATH):
             "mech_info": ([_P, _P], ctypes.c_int),
             "mech_grid": ([_P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
             "mech_destroy": ([_P], ctypes.c_int),
+            "mech_diffusion_create": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_double, _P, _P], ctypes.c_int),
+            "mech_diffusion_destroy": ([_P], ctypes.c_int),
+            "mech_diffusion_set_stream": ([_P, _P], ctypes.c_int),
+            "mech_diffusion_write": ([_P, _P], ctypes.c_int),
+            "mech_diffusion_read": ([_P, _P], ctypes.c_int),
+            "mech_diffusion_step": ([_P, ctypes.c_double, ctypes.c_int64], ctypes.c_int),
+            "mech_diffusion_gradient": ([_P, _P], ctypes.c_int),
+            "mech_diffusion_sync": ([_P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -497,6 +508,61 @@ class Mech:
     def close(self):
         if getattr(self, "h", None) is not None:
             mech_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Diffusion:
+    """One substrate-diffusion handle: S densities on an nx x ny x nz voxel
+    grid (arrays shaped (S, nz, ny, nx)), no-flux faces."""
+
+    def __init__(self, shape, dx, D, lam):
+        nz, ny, nx = (int(v) for v in shape)
+        D = _f64(D).reshape(-1)
+        lam = _f64(lam, D.size)
+        self.shape = (D.size, nz, ny, nx)
+        self.h = ctypes.c_void_p()
+        _check(load_library().mech_diffusion_create(ctypes.byref(self.h), nx, ny, nz, int(D.size), float(dx),
+                                                    _ptr(D), _ptr(lam)), "mech_diffusion_create")
+
+    def write(self, rho):
+        rho = _f64(rho, int(np.prod(self.shape)))
+        _check(load_library().mech_diffusion_write(self.h, _ptr(rho)), "mech_diffusion_write")
+
+    def read(self):
+        out = np.empty(self.shape)
+        _check(load_library().mech_diffusion_read(self.h, _ptr(out)), "mech_diffusion_read")
+        return out
+
+    def step(self, dt, n=1):
+        _check(load_library().mech_diffusion_step(self.h, float(dt), int(n)), "mech_diffusion_step")
+
+    def gradient(self):
+        S, nz, ny, nx = self.shape
+        out = np.empty((S, 3, nz, ny, nx))
+        _check(load_library().mech_diffusion_gradient(self.h, _ptr(out)), "mech_diffusion_gradient")
+        return out
+
+    def set_stream(self, stream):
+        _check(load_library().mech_diffusion_set_stream(self.h, ctypes.c_void_p(stream)), "mech_diffusion_set_stream")
+
+    def sync(self):
+        _check(load_library().mech_diffusion_sync(self.h), "mech_diffusion_sync")
+
+    def close(self):
+        if self.h:
+            load_library().mech_diffusion_destroy(self.h)
             self.h = None
 
     def __enter__(self):
