@@ -93,6 +93,8 @@ def parse():
                    help="single populations: also time a loop in which this fraction of the cells dies every "
                         "--turnover-every steps and as many daughters are added next to random survivors")
     p.add_argument("--turnover-every", type=int, default=10)
+    p.add_argument("--substrates", type=int, default=4,
+                   help="--workload diffusion_75: substrates on the 75^3-voxel grid")
     return p.parse_args()
 
 
@@ -250,6 +252,24 @@ def run_reference(args):
     import oracle
     from paper_2306_11544_gb300 import synth
     oracle.build()
+    if args.workload == "diffusion_75":  # the diffusion oracle on the same field, one host core
+        shape, dx, dt, D, lam, rho = diffusion_workload(max(1, args.substrates))
+        steps = max(1, min(args.steps, 20))
+        rho = oracle.diffusion_step(rho, D, lam, dx, dt, max(0, min(args.warmup, 3)))
+        t0 = time.perf_counter()
+        oracle.diffusion_step(rho, D, lam, dx, dt, steps)
+        t = time.perf_counter() - t0
+        nvals = int(np.prod(shape))
+        value = nvals * steps / t
+        line = {"impl": "reference", "metric": DIFF_METRIC, "value": value, "unit": DIFF_UNIT, "n_gpus": args.gpus,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "diffusion_75", "grid": list(shape[1:]), "substrates": shape[0]},
+                "cpu_baseline": {"value": value, "unit": DIFF_UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{steps} oracle steps of the {shape[0]} x 75^3 field"},
+                "e2e": {"value": value, "unit": DIFF_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     scale = args.scale * (1.0 / 64.0 if args.workload == "clustered_20m" else 0.05)
     pop = make_workload(args.workload, scale)
     reps = [pop] if isinstance(pop, synth.Population) else pop.reps
@@ -295,6 +315,103 @@ def cpu_baseline(pop):
     t = time.perf_counter() - t0
     return {"value": n / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"one full oracle step (bin+force+AB2, FP64) of all {n} cells, {t:.1f} s"}
+
+
+DIFF_METRIC = "substrate diffusion voxel-updates/s (3 implicit line solves per step, FP64)"
+DIFF_UNIT = "voxel-updates/s"
+
+
+def diffusion_workload(S):
+    """The paper's 75^3-voxel microenvironment (Sec. 5.2) with S substrates:
+    20 um voxels, dt 0.01 min, diffusion coefficients from 1e5 um^2/min (an
+    oxygen-like substrate) down by a factor 10 per substrate, decay 0.1/min,
+    and a seeded field (a smooth bump on uniform noise)."""
+    shape = (S, 75, 75, 75)
+    D = 1e5 / 10.0 ** np.arange(S)
+    lam = np.full(S, 0.1)
+    rng = np.random.Generator(np.random.PCG64(0))
+    z, y, x = np.meshgrid(*(np.arange(75),) * 3, indexing="ij")
+    rho = rng.random(shape) + 5.0 * np.exp(-((x - 30) ** 2 + (y - 45) ** 2 + (z - 37) ** 2) / 50.0)[None]
+    return shape, 20.0, 0.01, D, lam, rho
+
+
+def run_diffusion(args):
+    """Benchmark of the substrate diffusion solver (one JSON line, the same
+    keys as the mechanics line)."""
+    import torch
+    from paper_2306_11544_gb300 import build as libbuild
+    from paper_2306_11544_gb300 import mech
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    mech.load_library()
+    shape, dx, dt, D, lam, rho = diffusion_workload(max(1, args.substrates))
+    S = shape[0]
+    nv = int(np.prod(shape[1:]))
+    stream = torch.cuda.Stream()
+    with mech.Diffusion(shape[1:], dx, D, lam) as d:
+        d.set_stream(stream.cuda_stream)
+        d.write(rho)
+        d.step(dt, args.warmup)
+        d.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(local, enabled=not args.no_clocks) as clocks:
+            ev0.record(stream)
+            d.step(dt, args.steps)
+            ev1.record(stream)
+            ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        t = reduce_max(ms, None, "cuda")
+        value = S * nv * args.steps / (t * 1e-3) * ws
+        # end to end: densities in from pinned host memory, one step, densities out
+        e2e = None
+        if not args.no_e2e:
+            host = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+            host[...] = d.read()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                d.write(host)
+                d.step(dt, 1)
+                host[...] = d.read()
+            te = time.perf_counter() - t0
+            e2e = {"value": S * nv * args.e2e_steps / te, "unit": DIFF_UNIT, "h2d_bytes_per_step": 8 * S * nv,
+                   "d2h_bytes_per_step": 8 * S * nv, "steps": args.e2e_steps,
+                   "path": "mech_diffusion_write -> mech_diffusion_step(1) -> mech_diffusion_read (pinned host)"}
+    peak, peak_kind = hbm_peak()
+    bytes_step = 3 * 16 * S * nv  # each of the three solves reads and writes every value once
+    step_s = t * 1e-3 / args.steps
+    line = {
+        "metric": DIFF_METRIC, "value": value, "unit": DIFF_UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "diffusion_75", "grid": list(shape[1:]), "substrates": S, "voxel_um": dx,
+                   "dt_min": dt, "D_um2_per_min": [float(v) for v in D], "decay_per_min": [float(v) for v in lam],
+                   "l2": f"no flush: the {8 * S * nv / 1e6:.1f} MB of densities stay in the 129 MB L2, as they "
+                         f"would between the solves of a simulation step"},
+        "roofline": {"bound": "latency", "kernel": "k_diff_x_tiled + 2 x k_diff_yz per step",
+                     "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bytes_step / step_s / 1e9 / peak, "traffic": None,
+                     "model": "48 B per voxel value per step (each solve reads and writes it once); the "
+                              "recurrences along every grid line are sequential, so the kernels are bound by "
+                              "the latency of their dependent steps, not by bandwidth",
+                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        k = 2
+        t0 = time.perf_counter()
+        oracle.diffusion_step(rho, D, lam, dx, dt, k)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S * nv * k / tc, "unit": DIFF_UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{k} oracle steps of the same {S} x 75^3 field, {tc:.2f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def oracle_timing(args):
@@ -481,6 +598,8 @@ def main():
         return precision_study(args)
     if args.oracle_timing:
         return oracle_timing(args)
+    if args.workload == "diffusion_75":
+        return run_diffusion(args)
     ws, rank, local = dist_env()
     import torch
     from paper_2306_11544_gb300 import build as libbuild
