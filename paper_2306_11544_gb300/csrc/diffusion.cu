@@ -11,10 +11,13 @@
 //   e = lambda dt / 3, the tridiagonal system has diagonal 1 + 2k + e inside,
 //   1 + k + e at the two faces (a mirrored neighbour: no flux), 1 + e for
 //   n = 1, and off-diagonals -k.  It is solved by the Thomas algorithm with
-//   coefficients shared by all lines of an axis:
-//      m_0 = T_00;  c_i = -k / m_i;  m_i = T_ii + k c_{i-1}   (i >= 1)
-//      forward  r_0 = old_0 / m_0;  r_i = (old_i + k r_{i-1}) / m_i
+//   coefficients shared by all lines of an axis, the pivots inverted once:
+//      m_0 = T_00;  m_i = T_ii + k c_{i-1} (i >= 1);  w_i = 1 / m_i;
+//      c_i = -k w_i
+//      forward  r_0 = old_0 w_0;  r_i = (old_i + k r_{i-1}) w_i
 //      backward r_i = r_i - c_i r_{i+1}   (i = n-2 .. 0)
+//   (no division inside the recurrences: an FP64 division costs about six
+//   FP64 additions on this GPU)
 //   in FP64 with IEEE operations in this order (no contraction), so every
 //   value is reproducible.  Gradients: central differences inside, one-sided
 //   at the faces, zero along an axis of one voxel; array [s][axis][v].
@@ -49,8 +52,8 @@ namespace {
 constexpr int kLineTile = 32;   // x lines staged per warp
 constexpr int kMaxNxTile = 191;  // 32 lines of up to 191 doubles (+1 pad) fit in 48 KB of shared memory
 
-// Thomas coefficients of every (substrate, axis): m and c, nmax each; and k
-// per substrate.  One thread per (substrate, axis).
+// Thomas coefficients of every (substrate, axis): reciprocal pivots w (in m)
+// and c, nmax each; and k per substrate.  One thread per (substrate, axis).
 __global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx, double dt,
                               const double* __restrict__ D, const double* __restrict__ lam, double* __restrict__ m,
                               double* __restrict__ c, double* __restrict__ kk) {
@@ -68,18 +71,20 @@ __global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int
         if (n == 1) diag = __dadd_rn(1.0, e);
         else if (i == 0 || i == n - 1) diag = __dadd_rn(__dadd_rn(1.0, k), e);
         else diag = __dadd_rn(__dadd_rn(1.0, __dmul_rn(2.0, k)), e);
-        mm[i] = i == 0 ? diag : __dadd_rn(diag, __dmul_rn(k, cc[i - 1]));
-        if (i < n - 1) cc[i] = __ddiv_rn(-k, mm[i]);
+        const double piv = i == 0 ? diag : __dadd_rn(diag, __dmul_rn(k, cc[i - 1]));
+        mm[i] = __ddiv_rn(1.0, piv);
+        if (i < n - 1) cc[i] = __dmul_rn(-k, mm[i]);
     }
 }
 
-// One line of n values at p[0], p[stride], ... in place (any memory space).
-__device__ __forceinline__ void thomas(double* p, int64_t stride, int64_t n, double k, const double* __restrict__ m,
+// One line of n values at p[0], p[stride], ... in place (any memory space);
+// w holds the reciprocal pivots.
+__device__ __forceinline__ void thomas(double* p, int64_t stride, int64_t n, double k, const double* __restrict__ w,
                                        const double* __restrict__ c) {
-    double prev = __ddiv_rn(p[0], m[0]);
+    double prev = __dmul_rn(p[0], w[0]);
     p[0] = prev;
     for (int64_t i = 1; i < n; ++i) {
-        prev = __ddiv_rn(__dadd_rn(p[i * stride], __dmul_rn(k, prev)), m[i]);
+        prev = __dmul_rn(__dadd_rn(p[i * stride], __dmul_rn(k, prev)), w[i]);
         p[i * stride] = prev;
     }
     double next = prev;
