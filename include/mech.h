@@ -25,6 +25,11 @@
  * The paper names these regions but prints none of the formulas; the force
  * law and the integrator above are the problem this library solves.
  *
+ * Beyond the step: cells removed and added between steps (mech_remove_cells,
+ * mech_add_cells, mech_add_cells_batch), and a substrate diffusion solver
+ * with gradients for the microenvironment regions of Sec. 5.1-5.2
+ * (mech_diffusion_*), both described with their calls below.
+ *
  * Units: um and min.  All per-cell arrays are in the CALLER's cell order
  * (index 0..n-1, concatenated over replicates for a batch); positions and
  * velocities are interleaved xyz, 3*n doubles.  The library copies every
