@@ -23,12 +23,13 @@
  *   (for n = 1: (1 + e) r_0 = old_0), the face rows being the interior rows
  *   with a mirrored neighbour (no flux through the face).
  *
- *   The solve is the Thomas algorithm with the reciprocal pivots formed once
- *   per axis, in this order and in FP64 with no contraction:
- *      m_0 = T_00;  m_i = T_ii + k c_{i-1} (i >= 1);  w_i = 1 / m_i;
- *      c_i = -k w_i
- *      forward  r_0 = old_0 w_0;  r_i = (old_i + k r_{i-1}) w_i
+ *   The solve is the textbook Thomas algorithm (forward elimination, then
+ *   back substitution), dividing by each pivot, in FP64 with no contraction:
+ *      m_0 = T_00;  c_i = -k / m_i;  m_i = T_ii + k c_{i-1}   (i >= 1)
+ *      forward  r_0 = old_0 / m_0;  r_i = (old_i + k r_{i-1}) / m_i
  *      backward r_i = r_i - c_i r_{i+1}   (i = n-2 .. 0)
+ *   (Any other arrangement of the same elimination, e.g. multiplying by
+ *   reciprocal pivots, agrees with this one to rounding only.)
  *
  *   Gradient of rho_s along each axis: central differences
  *   (rho[i+1] - rho[i-1]) / (2 dx) inside, one-sided differences at the two
@@ -40,23 +41,22 @@
 #include <stdint.h>
 #include <stdlib.h>
 
-/* Thomas coefficients of one axis: reciprocal pivots w[0..n), c[0..n-1). */
-static void coefficients(int64_t n, double k, double e, double* w, double* c) {
+/* Thomas coefficients of one axis: pivots m[0..n), c[0..n-1). */
+static void coefficients(int64_t n, double k, double e, double* m, double* c) {
     for (int64_t i = 0; i < n; ++i) {
         double diag;
         if (n == 1) diag = 1.0 + e;
         else if (i == 0 || i == n - 1) diag = 1.0 + k + e;
         else diag = 1.0 + 2.0 * k + e;
-        const double m = i == 0 ? diag : diag + k * c[i - 1];
-        w[i] = 1.0 / m;
-        if (i < n - 1) c[i] = -k * w[i];
+        m[i] = i == 0 ? diag : diag + k * c[i - 1];
+        if (i < n - 1) c[i] = -k / m[i];
     }
 }
 
 /* One line of n values at p[0], p[stride], ... solved in place. */
-static void solve_line(double* p, int64_t stride, int64_t n, double k, const double* w, const double* c) {
-    p[0] = p[0] * w[0];
-    for (int64_t i = 1; i < n; ++i) p[i * stride] = (p[i * stride] + k * p[(i - 1) * stride]) * w[i];
+static void solve_line(double* p, int64_t stride, int64_t n, double k, const double* m, const double* c) {
+    p[0] = p[0] / m[0];
+    for (int64_t i = 1; i < n; ++i) p[i * stride] = (p[i * stride] + k * p[(i - 1) * stride]) / m[i];
     for (int64_t i = n - 2; i >= 0; --i) p[i * stride] = p[i * stride] - c[i] * p[(i + 1) * stride];
 }
 

@@ -17,9 +17,9 @@
 //      forward  r_0 = old_0 w_0;  r_i = (old_i + k r_{i-1}) w_i
 //      backward r_i = r_i - c_i r_{i+1}   (i = n-2 .. 0)
 //   (no division inside the recurrences: an FP64 division costs about six
-//   FP64 additions on this GPU)
-//   in FP64 with IEEE operations in this order (no contraction), so every
-//   value is reproducible.  Gradients: central differences inside, one-sided
+//   FP64 additions on this GPU; the plain elimination divides by m_i, and the
+//   two arrangements agree to rounding), in FP64 with IEEE operations in this
+//   order (no contraction), so every value is reproducible run to run.  Gradients: central differences inside, one-sided
 //   at the faces, zero along an axis of one voxel; array [s][axis][v].
 //
 // GB300 mapping: the work is a set of independent recurrences (one per grid
@@ -52,14 +52,11 @@ namespace {
 constexpr int kLineTile = 32;   // x lines staged per warp
 constexpr int kMaxNxTile = 191;  // 32 lines of up to 191 doubles (+1 pad) fit in 48 KB of shared memory
 
-// Thomas coefficients of every (substrate, axis): reciprocal pivots w (in m)
-// and c, nmax each; and k per substrate.  One thread per (substrate, axis).
-__global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx, double dt,
-                              const double* __restrict__ D, const double* __restrict__ lam, double* __restrict__ m,
-                              double* __restrict__ c, double* __restrict__ kk) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * S) return;
-    const int s = t / 3, a = t - 3 * s;
+// Thomas coefficients of one (substrate, axis) pair t = 3 s + axis.
+__device__ __forceinline__ void coeffs_one(int64_t t, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx,
+                                           double dt, const double* __restrict__ D, const double* __restrict__ lam,
+                                           double* __restrict__ m, double* __restrict__ c, double* __restrict__ kk) {
+    const int64_t s = t / 3, a = t - 3 * s;
     const int64_t n = a == 0 ? nx : (a == 1 ? ny : nz);
     const double k = __ddiv_rn(__dmul_rn(D[s], dt), __dmul_rn(dx, dx));
     const double e = __ddiv_rn(__dmul_rn(lam[s], dt), 3.0);
@@ -75,6 +72,17 @@ __global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int
         mm[i] = __ddiv_rn(1.0, piv);
         if (i < n - 1) cc[i] = __dmul_rn(-k, mm[i]);
     }
+}
+
+// Thomas coefficients of every (substrate, axis): reciprocal pivots w (in m)
+// and c, nmax each; and k per substrate.  A grid-stride loop over the 3 S
+// (substrate, axis) pairs, one thread each.
+__global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx, double dt,
+                              const double* __restrict__ D, const double* __restrict__ lam, double* __restrict__ m,
+                              double* __restrict__ c, double* __restrict__ kk) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * (int64_t)S;
+         t += (int64_t)gridDim.x * blockDim.x)
+        coeffs_one(t, nx, ny, nz, nmax, dx, dt, D, lam, m, c, kk);
 }
 
 // One line of n values at p[0], p[stride], ... in place (any memory space);
@@ -288,12 +296,10 @@ int mech_diffusion_create(mech_diffusion_t** out, int64_t nx, int64_t ny, int64_
     if (rc == MECH_OK) rc = dcuda(cudaMemsetAsync(h->d_rho, 0, nvals * 8, h->stream), "zero densities");
     if (rc == MECH_OK) rc = dcuda(cudaStreamSynchronize(h->stream), "create");
     if (rc != MECH_OK) return bail(rc);
-    if (h->nx <= kMaxNxTile) {
-        const int bytes = (int)(kLineTile * (h->nx | 1) * sizeof(double));
-        rc = dcuda(cudaFuncSetAttribute(k_diff_x_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-                   "cudaFuncSetAttribute");
-        if (rc != MECH_OK) return bail(rc);
-    }
+    // the staged x tile needs at most 32 x 191 doubles = 48,896 bytes, within
+    // the default 48 KiB of dynamic shared memory: no per-function attribute
+    // (a process-wide setting) is changed
+    static_assert(kLineTile * kMaxNxTile * sizeof(double) <= 48 * 1024, "x tile within the default limit");
     *out = h;
     return MECH_OK;
 }

@@ -20,12 +20,13 @@ MUTANTS = [
     ("face_rows_interior", "else if (i == 0 || i == n - 1) diag = 1.0 + k + e;", "else if (0) diag = 1.0 + k + e;"),
     ("face_rows_without_k", "else if (i == 0 || i == n - 1) diag = 1.0 + k + e;",
      "else if (i == 0 || i == n - 1) diag = 1.0 + e;"),
-    ("pivot_not_eliminated", "const double m = i == 0 ? diag : diag + k * c[i - 1];", "const double m = diag;"),
-    ("pivot_wrong_sign", "const double m = i == 0 ? diag : diag + k * c[i - 1];",
-     "const double m = i == 0 ? diag : diag - k * c[i - 1];"),
-    ("c_sign", "if (i < n - 1) c[i] = -k * w[i];", "if (i < n - 1) c[i] = k * w[i];"),
-    ("forward_sign", "p[i * stride] = (p[i * stride] + k * p[(i - 1) * stride]) * w[i];",
-     "p[i * stride] = (p[i * stride] - k * p[(i - 1) * stride]) * w[i];"),
+    ("pivot_not_eliminated", "m[i] = i == 0 ? diag : diag + k * c[i - 1];", "m[i] = diag;"),
+    ("pivot_wrong_sign", "m[i] = i == 0 ? diag : diag + k * c[i - 1];",
+     "m[i] = i == 0 ? diag : diag - k * c[i - 1];"),
+    ("c_sign", "if (i < n - 1) c[i] = -k / m[i];", "if (i < n - 1) c[i] = k / m[i];"),
+    ("forward_sign", "p[i * stride] = (p[i * stride] + k * p[(i - 1) * stride]) / m[i];",
+     "p[i * stride] = (p[i * stride] - k * p[(i - 1) * stride]) / m[i];"),
+    ("first_pivot_skipped", "p[0] = p[0] / m[0];", "p[0] = p[0];"),
     ("backward_skips_first", "for (int64_t i = n - 2; i >= 0; --i)", "for (int64_t i = n - 2; i >= 1; --i)"),
     ("k_uses_dx", "const double k = D[s] * dt / (dx * dx);", "const double k = D[s] * dt / dx;"),
     ("decay_not_split", "const double e = lambda[s] * dt / 3.0;", "const double e = lambda[s] * dt;"),
