@@ -19,10 +19,22 @@ What pins what:
                        on a dyadic grid), 90-degree rotations, the equilibrium
                        of a simple cubic lattice at the two-cell equilibrium
                        spacing.
+  * FP32 keys       -> the same faces on a dyadic grid decided in FP32 (every
+                       operation exact there, so a cell on a face goes to the
+                       higher voxel in FP32 too).
+  * subset velocity -> its rows equal the full binned velocity's rows of the
+                       listed cells (any order, repeats, empty list).
+  * force law       -> the scalar force of two like cells evaluated by hand
+                       at d = 10, 18, 20 um with the 2,000-cell spheroid's
+                       parameters (R 8.41, ccr 10, cca 0.4, A 1.25):
+                       1.534069, -0.0082802, -0.00095068 um/min.
   * integrator      -> the linear contraction rate of two cells relaxing to
                        equilibrium equals the dominant root of the AB2
                        characteristic polynomial built from the analytic
-                       slope of the force at equilibrium.
+                       slope of the force at equilibrium; the separation of
+                       two cells follows the scalar two-step recursion
+                       s_{n+1} = s_n + dt (3 f(s_n) - f(s_{n-1})), f(s_{-1}) = 0,
+                       with f written out here from the force law.
 """
 from __future__ import annotations
 
@@ -112,6 +124,29 @@ def pin_keys_f32(o):
     assert np.array_equal(k64, k32)
 
 
+def pin_keys_f32_faces(o):
+    """FP32 decision at exact faces: with lo and h powers of two (times small
+    integers) every FP32 operation of the index is exact, so a coordinate on
+    a face lands in the higher voxel, as the FP64 rule does."""
+    h = 0.5
+    lo = np.array([-2.0, 0.0, 4.0])
+    dims = np.array([16, 8, 6], np.int32)
+    pts = np.array([[-2.0, 0.0, 4.0], [-1.5, 0.5, 4.5], [0.0, 3.5, 6.5], [5.5, 0.25, 5.0],
+                    [-1.75, 3.75, 6.75], [1.0, 1.0, 5.5]], np.float32)
+    expect = [(0, 0, 0), (1, 1, 1), (4, 7, 5), (15, 0, 2), (0, 7, 5), (6, 2, 3)]
+    k32 = o.keys_f32(pts, lo, h, dims).astype(np.int64)
+    k64 = o.keys(pts.astype(np.float64), lo, h, dims).astype(np.int64)
+    for kk, kd, (ex, ey, ez) in zip(k32, k64, expect):
+        want = ex + int(dims[0]) * (ey + int(dims[1]) * ez)
+        assert kk == want, (kk, want)
+        assert kd == want, (kd, want)
+    # one FP32 ulp below a face stays in the lower voxel (lo = 0, so the
+    # subtraction cannot round it up onto the face)
+    below = np.nextafter(np.float32(1.5), np.float32(0.0))
+    kb = o.keys_f32(np.array([[below, 0.75, 1.25]], np.float32), np.zeros(3), h, dims)
+    assert int(kb[0]) == 2 + int(dims[0]) * (1 + int(dims[1]) * 2), int(kb[0])
+
+
 def pin_counting_sort(o):
     rng = np.random.Generator(np.random.PCG64(13))
     for n, V in [(0, 5), (1, 1), (1000, 37), (5000, 4000)]:
@@ -163,6 +198,22 @@ def pin_neighbour_set(o):
         assert len(a) == p_bin.shape[0]
         assert a == b, (len(a), len(b))
         assert len(b) > 0
+
+
+def pin_velocities_subset(o):
+    """Rows of the subset routine are the full routine's rows of the listed
+    cells, for an unsorted list with repeats, and for an empty list."""
+    xyz, R, ccr, cca, lo, h, dims = _pin_populations()[4]
+    full = o.velocities(xyz, R, ccr, cca, A_CFG, lo, h, dims)
+    rng = np.random.Generator(np.random.PCG64(19))
+    idx = rng.integers(0, xyz.shape[0], size=57)
+    idx[3] = idx[10]
+    idx[-1] = xyz.shape[0] - 1
+    sub = o.velocities_subset(xyz, R, ccr, cca, A_CFG, lo, h, dims, idx)
+    assert sub.shape == (idx.size, 3)
+    assert np.array_equal(sub, full[idx])
+    empty = o.velocities_subset(xyz, R, ccr, cca, A_CFG, lo, h, dims, np.zeros(0, np.int64))
+    assert empty.shape == (0, 3)
 
 
 def pin_binned_velocity(o):
@@ -219,6 +270,21 @@ def pin_two_cell(o):
     assert np.array_equal(v[0], -v[1])
     f, _, _ = _scalar_force(o, S2, Ri=Ri, Rj=Rj, ccr=ccr, cca=cca)
     assert abs(f - (-Ca * (1.0 - 1.0 / A_CFG) ** 2)) < 1e-13
+
+
+# f(d) of two like cells with R 8.41 um, ccr 10, cca 0.4 (um/min), A 1.25,
+# evaluated by hand from the force law: S = 16.82, A S = 21.025;
+# f(10) = 10 (1 - 10/16.82)^2 - 0.4 (1 - 10/21.025)^2, f(18) and f(20) have
+# d > S, so only the adhesion bracket is left.
+TWO_CELL_VALUES = [(10.0, 1.534069, 5e-7), (18.0, -0.0082802, 5e-8), (20.0, -0.00095068, 5e-9)]
+
+
+def pin_two_cell_values(o):
+    for d, f_ref, tol in TWO_CELL_VALUES:
+        for e in ((1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.48, 0.6, -0.64)):
+            f, v, _ = _scalar_force(o, d, direction=e)
+            assert abs(f - f_ref) <= tol, (d, f, f_ref)
+            assert np.array_equal(v[0], -v[1])
 
 
 def pin_c1_at_cutoffs(o):
@@ -339,6 +405,38 @@ def pin_ab2_relaxation_rate(o):
     assert np.abs(mid - 0.5 * (xyz[0] + xyz[1])).max() < 1e-12
 
 
+def _f_scalar(s, S, Cr, Ca, A):
+    """Scalar pair force of the force law, written out independently here."""
+    if not (0.0 < s < A * S):
+        return 0.0
+    rep = Cr * (1.0 - s / S) ** 2 if s < S else 0.0
+    return rep - Ca * (1.0 - s / (A * S)) ** 2
+
+
+def pin_ab2_scalar_recursion(o):
+    """Two like cells on the x axis, symmetric about the origin: each moves by
+    dt (1.5 v_n - 0.5 v_{n-1}) with v = +-f(s) along the axis, so the
+    separation obeys s_{n+1} = s_n + dt (3 f(s_n) - f(s_{n-1})), f(s_{-1}) = 0.
+    Started from both sides of the equilibrium (and from beyond S); the
+    oracle's separation must follow the recursion to rounding."""
+    S = 2 * R_CFG
+    dt = 0.1
+    lo = np.full(3, -60.0)
+    dims = np.array([4, 4, 4])
+    for s0, steps in ((12.0, 60), (19.5, 60), (16.5, 25)):
+        xyz = np.array([[0.5 * s0, 0.0, 0.0], [-0.5 * s0, 0.0, 0.0]])
+        R, ccr, cca = np.full(2, R_CFG), np.full(2, CCR_CFG), np.full(2, CCA_CFG)
+        x, _, _ = o.run(xyz, R, ccr, cca, A_CFG, lo, 30.0, dims, dt, steps)
+        s, f_prev = s0, 0.0
+        for _ in range(steps):
+            f_now = _f_scalar(s, S, CCR_CFG, CCA_CFG, A_CFG)
+            s, f_prev = s + dt * (3.0 * f_now - f_prev), f_now
+        got = x[0, 0] - x[1, 0]
+        assert abs(got - s) <= 1e-14 * s, (s0, got, s, got - s)
+        assert np.all(x[:, 1:] == 0.0)
+        assert abs(x[0, 0] + x[1, 0]) <= 1e-13
+
+
 def pin_ab2_start(o):
     """First step of AB2 with v_{-1} = 0, second step with the stored v."""
     xyz, R, ccr, cca, e = _two_cells(14.0)
@@ -362,6 +460,7 @@ def pin_special_sizes(o):
     assert np.all(v == 0.0)
 
 
-ALL_PINS = [pin_keys, pin_keys_f32, pin_counting_sort, pin_neighbour_set, pin_binned_velocity,
-            pin_two_cell, pin_c1_at_cutoffs, pin_zero_net_velocity, pin_translation, pin_rotation,
-            pin_lattice, pin_ab2_relaxation_rate, pin_ab2_start, pin_special_sizes]
+ALL_PINS = [pin_keys, pin_keys_f32, pin_keys_f32_faces, pin_counting_sort, pin_neighbour_set,
+            pin_velocities_subset, pin_binned_velocity, pin_two_cell, pin_two_cell_values, pin_c1_at_cutoffs,
+            pin_zero_net_velocity, pin_translation, pin_rotation, pin_lattice, pin_ab2_relaxation_rate,
+            pin_ab2_scalar_recursion, pin_ab2_start, pin_special_sizes]

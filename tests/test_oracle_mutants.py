@@ -38,6 +38,16 @@ MUTANTS = [
     ("ab2_wrong_weights", "xyz[k] = xyz[k] + dt * (1.5 * v[k] - 0.5 * vprev[k]);",
      "xyz[k] = xyz[k] + dt * (1.5 * v[k] + 0.5 * vprev[k]);", 0),
     ("vprev_not_updated", "vprev[k] = v[k];", "(void)0;", 0),
+    # caught by the new pins: FP32 face decision, subset indexing, the
+    # hand-evaluated two-cell values, the scalar AB2 recursion
+    ("f32_face_to_lower_voxel", "float f = floorf(t);", "float f = ceilf(t) - 1.0f;", 0),
+    ("subset_rows_by_cell", "velocity_one(idx[k], &b, xyz, R, ccr, cca, A, &v[3 * k]);",
+     "velocity_one(idx[k], &b, xyz, R, ccr, cca, A, &v[3 * (k > 0 ? k - 1 : k)]);", 0),
+    ("subset_ignores_list", "velocity_one(idx[k], &b, xyz, R, ccr, cca, A, &v[3 * k]);",
+     "velocity_one(k, &b, xyz, R, ccr, cca, A, &v[3 * k]);", 0),
+    ("adhesion_cubed", "c = c - sqrt(ccai * ccaj) * (ta * ta);", "c = c - sqrt(ccai * ccaj) * (ta * ta * ta);", 0),
+    ("ab2_first_step_euler_weight", "xyz[k] = xyz[k] + dt * (1.5 * v[k] - 0.5 * vprev[k]);",
+     "xyz[k] = xyz[k] + dt * (1.5 * v[k] - 0.45 * vprev[k]);", 0),
 ]
 
 
