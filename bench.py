@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--tile", default="4,4,4",
                    help="voxel tile for dense regions (4,4,4, 4,4,8 or 8,4,4), or 0 for none")
     p.add_argument("--dense-min", type=int, default=12)
+    p.add_argument("--dense-kernel", default="warp_per_voxel", choices=["warp_per_voxel", "block_per_tile"],
+                   help="kernel for the cells of dense tiles")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,7 +232,7 @@ def make_workload(name, scale):
 def describe(pop_or_ens, name, args, n, V):
     from paper_2306_11544_gb300 import synth
     cfg = {"workload": name, "cells": n, "voxels": V, "mode": args.mode, "scale": args.scale,
-           "tile": args.tile, "dense_min": args.dense_min}
+           "tile": args.tile, "dense_min": args.dense_min, "dense_kernel": args.dense_kernel}
     if isinstance(pop_or_ens, synth.Population):
         p = pop_or_ens
         cfg.update({"voxel_um": p.h, "internal_voxel_um": getattr(args, "voxel_value", p.h), "dt_min": p.dt, "A": p.A,
@@ -647,6 +649,7 @@ def main():
         m.set_launch(args.block)
     tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
     m.set_tiling(tile, args.dense_min)
+    m.set_dense_kernel(args.dense_kernel)
     tuned = None
     if args.autotune:
         from paper_2306_11544_gb300 import autotune

@@ -74,6 +74,7 @@ struct mech {
     // voxel tiles
     int ltx = 2, lty = 2, ltz = 2;
     bool use_tiles = true;
+    int tile_kernel = kTileKernelVox;
     uint32_t dense_min = 12;
     uint32_t NT = 0;
     size_t tcap = 0;
@@ -214,6 +215,7 @@ struct mech {
         a.lty = lty;
         a.ltz = ltz;
         a.use_tiles = use_tiles ? 1 : 0;
+        a.tile_kernel = tile_kernel;
         a.ntiles = NT;
         a.dense_min = dense_min;
         a.tcount_cur = d_tcount[a_idx];
@@ -843,6 +845,19 @@ int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t tile_z, i
     }
     h->invalidate_graphs();
     if (h->params_set && h->grid_dirty) return build_grids(h);
+    return MECH_OK;
+}
+
+int mech_set_dense_kernel(mech_t* h, int32_t kernel) {
+    MECH_TRY(check_handle(h));
+    if (kernel != MECH_DENSE_WARP_PER_VOXEL && kernel != MECH_DENSE_BLOCK_PER_TILE)
+        return fail(MECH_E_ARG, "dense kernel must be MECH_DENSE_WARP_PER_VOXEL or MECH_DENSE_BLOCK_PER_TILE");
+    const int k = kernel == MECH_DENSE_WARP_PER_VOXEL ? kTileKernelVox : kTileKernelCTA;
+    if (k != h->tile_kernel) {
+        h->tile_kernel = k;
+        h->tile_grid = tile_kernel_grid(h->args(0, 1), h->sms);
+        h->invalidate_graphs();
+    }
     return MECH_OK;
 }
 

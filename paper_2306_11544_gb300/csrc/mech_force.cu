@@ -144,17 +144,17 @@ struct Acc3 {
 
 // Pair term (FP32) for a candidate at offset r = x_i - x_j, given as an exact
 // hi part h (a difference of values on the q grid) plus a small lo part l;
-// Rlo is the sum of the two radius residuals R - (float)R.  Adds
-// (c_r - c_a) r / d if 0 < d < A S.
+// Rlo is the sum of the two radius residuals R - (float)R.  Sets f to
+// (c_r - c_a) r / d and returns true if 0 < d < A S (else f = 0, false).
 //   1 - d/S is formed as (S^2 - d^2) / (S (S + d)), with d^2 and S^2 carried
 //   as unevaluated sums (error-free products and sums), so the cancellation of
 //   1 - d/S near contact costs no accuracy: t and t_a are accurate to a few
 //   ulp even where d/S is close to 1, which a direct 1 - d/S is not.  The
 //   adhesion term uses (A S)^2 - d^2 = S^2 (A^2 - 1) + (S^2 - d^2), A2m1 being
 //   A^2 - 1 rounded once.
-__device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
-                                          float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
-                                          float A, float A2m1, Acc3& acc) {
+__device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
+                                           float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
+                                           float A, float A2m1, float3& f) {
     const float rx = hx + lx, ry = hy + ly, rz = hz + lz;
     const float d2 = rx * rx + ry * ry + rz * rz;
     float Se;
@@ -183,8 +183,18 @@ __device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx
             cf += (sccri * sccrj) * (t * t);
         }
         const float sc = cf * rd;
-        acc.add(sc * rx, sc * ry, sc * rz);
+        f = make_float3(sc * rx, sc * ry, sc * rz);
+        return true;
     }
+    f = make_float3(0.f, 0.f, 0.f);
+    return false;
+}
+
+__device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
+                                          float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
+                                          float A, float A2m1, Acc3& acc) {
+    float3 f;
+    if (pair_force(hx, hy, hz, lx, ly, lz, Ri, Rj, Rlo, sccri, sccai, sccrj, sccaj, A, A2m1, f)) acc.add(f.x, f.y, f.z);
 }
 
 // Squared candidate cutoff for a target with cut_i = A R_i + margin.
@@ -421,7 +431,7 @@ __global__ void k_tile_classify(const StepArgs a) {
         bool dense = false;
         if (valid) {
             dense = a.use_tiles && a.tcount_cur[t] >= a.dense_min;
-            if (dense) {
+            if (dense && a.tile_kernel == kTileKernelCTA) {
                 const int r = rep_of_tile(a.grids, a.nrep, t);
                 const GridDev& g = a.grids[r];
                 const uint32_t lt = t - g.tbase;
@@ -437,6 +447,282 @@ __global__ void k_tile_classify(const StepArgs a) {
         if (lane == 0 && m) off = atomicAdd(a.ndense, (uint32_t)__popc(m));
         off = __shfl_sync(0xFFFFFFFFu, off, 0);
         if (dense) a.tlist[off + __popc(m & lanemask_lt())] = t;
+    }
+}
+
+// ------------------------------------------------- voxel-warp kernel ----
+// Dense tiles, one warp per tile at a time (warps claim tiles from a cursor;
+// no block-level barrier anywhere, warps run independently), voxel by voxel
+// in mesh order (x fastest).  For one voxel:
+//   * its candidates are the cells of its 27-voxel neighbourhood: nine runs
+//     of the voxel-sorted records, one per (dz, dy) row, each covering the
+//     row's voxels x-1 .. x+1 (lanes 0..8 look up the nine runs in start[]
+//     and scan their lengths);
+//   * the lanes hold the candidates, 32 per chunk (up to four chunks stay in
+//     registers), in the definition's order: rows (dz, dy) lexicographic,
+//     voxel order inside a row;
+//   * the voxel's targets are taken one at a time (their record broadcast to
+//     all lanes); every lane tests its candidate against the target on the
+//     hi parts (branch-free, with the margin), and the hits are appended to a
+//     per-warp queue, target by target in candidate order;
+//   * whenever 32 hits are queued, each lane evaluates one exact pair term and
+//     a segmented reduction over the lanes sums the terms of each target (the
+//     tree is fixed by the queue, so every run gives the same bits); the sums
+//     enter per-target accumulators with a Kahan compensation;
+//   * after up to kVoxSlots targets the batch is closed: one lane per target
+//     applies AB2 and counts the next step's histograms.
+// Candidate tests cost no memory access (the candidate sits in a register and
+// the target is a broadcast), and the pair terms run with all 32 lanes busy
+// whatever the hit pattern.  The tile's voxels need not be interior: rows
+// and voxels outside the grid are empty runs.
+constexpr int kVoxWarps = 8;        // warps per block
+constexpr int kVoxMinBlocks = 3;    // blocks per SM (register cap of the launch bounds)
+constexpr int kVoxSlots = 64;       // targets per batch
+constexpr int kVoxCached = 3;       // candidate chunks kept in registers (96 candidates)
+constexpr int kVoxQueue = 32 * (kVoxCached + 1);  // queued hits: < 32 left + up to 32 per cached chunk
+
+struct VoxWarp {
+    uint32_t qj[kVoxQueue];    // B position of the candidate of each queued hit
+    uint32_t tq[kVoxSlots];    // B position of the target in each slot
+    float acc[6][kVoxSlots];   // per slot: velocity sums x, y, z and their Kahan compensations
+    uint32_t rdel[9];          // per non-empty candidate run: record index minus candidate index
+    uint8_t qs[kVoxQueue];     // target slot of each queued hit
+};
+
+// Exact pair terms of the first 32 queued hits (one per lane; fewer at the end
+// of a batch), summed per target slot into the accumulators; the remaining
+// hits move to the front of the queue.
+__device__ __noinline__ void vox_flush(const StepArgs& a, const GridDev& g, VoxWarp& w, uint32_t& qn) {
+    const uint32_t lane = threadIdx.x & 31u;
+    __syncwarp();
+    const uint32_t cnt = min(qn, 32u);
+    const bool valid = lane < cnt;
+    const uint32_t sl = valid ? (uint32_t)w.qs[lane] : 0x100u + lane;  // distinct dummy slots
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    if (valid) {
+        const uint32_t j = w.qj[lane];
+        const uint32_t qi = w.tq[sl];
+        const float4 pi = __ldg(&a.B.rec[2 * (size_t)qi]);
+        const float4 ci = __ldg(&a.B.rec[2 * (size_t)qi + 1]);
+        const float4 pj = __ldg(&a.B.rec[2 * (size_t)j]);
+        const float4 cj = __ldg(&a.B.rec[2 * (size_t)j + 1]);
+        const float4 li = record_lo(pi, ci, g.qs);
+        const float4 lj = record_lo(pj, cj, g.qs);
+        pair_force(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w,
+                   li.w + lj.w, ci.x, ci.y, cj.x, cj.y, a.A_f, a.A2m1_f, f);
+    }
+    // segmented suffix sums: slots are non-decreasing over the lanes, so a
+    // lane adds the partial sum o lanes up whenever that lane has its slot;
+    // the first lane of each slot ends with the slot's total
+    const uint32_t sl_up = __shfl_up_sync(0xFFFFFFFFu, sl, 1);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ox = __shfl_down_sync(0xFFFFFFFFu, f.x, o);
+        const float oy = __shfl_down_sync(0xFFFFFFFFu, f.y, o);
+        const float oz = __shfl_down_sync(0xFFFFFFFFu, f.z, o);
+        const uint32_t os = __shfl_down_sync(0xFFFFFFFFu, sl, o);
+        if (lane + (uint32_t)o < 32u && os == sl) {
+            f.x += ox;
+            f.y += oy;
+            f.z += oz;
+        }
+    }
+    if (valid && (lane == 0 || sl_up != sl)) {
+        Acc3::add1(w.acc[0][sl], w.acc[3][sl], f.x);
+        Acc3::add1(w.acc[1][sl], w.acc[4][sl], f.y);
+        Acc3::add1(w.acc[2][sl], w.acc[5][sl], f.z);
+    }
+    // move the rest to the front, 32 entries at a time (sources stay ahead of
+    // destinations)
+    const uint32_t rest = qn - cnt;
+    for (uint32_t b = 0; b < rest; b += 32u) {
+        __syncwarp();
+        const uint32_t k = b + lane;
+        uint32_t tj = 0, ts = 0;
+        if (k < rest) {
+            tj = w.qj[cnt + k];
+            ts = w.qs[cnt + k];
+        }
+        __syncwarp();
+        if (k < rest) {
+            w.qj[k] = tj;
+            w.qs[k] = (uint8_t)ts;
+        }
+    }
+    __syncwarp();
+    qn = rest;
+}
+
+// Closes a batch: the last queued hits, then AB2 for every slot (one lane per
+// target) and the next step's histograms; clears the accumulators.
+template <int MODE>
+__device__ __forceinline__ void vox_close(const StepArgs& a, const GridDev& g, VoxWarp& w, uint32_t& qn,
+                                          uint32_t& nslot) {
+    const uint32_t lane = threadIdx.x & 31u;
+    while (qn) vox_flush(a, g, w, qn);
+    for (uint32_t s0 = 0; s0 < nslot; s0 += 32u) {
+        const uint32_t s = s0 + lane;
+        const bool valid = s < nslot;
+        uint32_t q = 0, nkey = 0, ntile = 0;
+        if (valid) {
+            q = w.tq[s];
+            const float vx = __fsub_rn(w.acc[0][s], w.acc[3][s]);
+            const float vy = __fsub_rn(w.acc[1][s], w.acc[4][s]);
+            const float vz = __fsub_rn(w.acc[2][s], w.acc[5][s]);
+            int nix, niy, niz;
+            nkey = ab2_epilogue<MODE>(a, g, q, a_slot(a, q), vx, vy, vz, nix, niy, niz);
+            ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) w.acc[c][s] = 0.f;
+        }
+        next_step_counts(a, q, nkey, ntile, valid);
+    }
+    __syncwarp();
+    nslot = 0;
+}
+
+// Candidate runs of one voxel: run p (lane p < 9) covers the records of row
+// (dz, dy) = (p / 3 - 1, p % 3 - 1) from voxel x - 1 to x + 1.  Candidate c of
+// the voxel (c < L) is record c + rdel[r], r = the number of non-empty runs
+// that start at or before c, minus one.
+struct VoxRuns {
+    uint32_t L;        // candidates
+    uint32_t off;      // lane p < 9: first candidate index of run p
+    uint32_t len;      // lane p < 9: its length
+};
+
+__device__ __forceinline__ uint32_t vox_cand_index(const VoxWarp& w, const VoxRuns& R, uint32_t c0) {
+    const uint32_t lane = threadIdx.x & 31u;
+    // bit (off_p - c0) for each non-empty run starting inside this chunk
+    const bool ne = R.len != 0u;
+    const uint32_t bit = (ne && R.off >= c0 && R.off < c0 + 32u) ? 1u << (R.off - c0) : 0u;
+    const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, bit);
+    const uint32_t before = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, ne && R.off < c0));
+    const uint32_t le = lanemask_lt() | (1u << lane);
+    const uint32_t r = before + (uint32_t)__popc(starts & le) - 1u;
+    return c0 + lane + w.rdel[min(r, 8u)];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kVoxWarps * 32, kVoxMinBlocks) k_force_vox(const StepArgs a) {
+    __shared__ VoxWarp s_w[kVoxWarps];
+    const uint32_t lane = threadIdx.x & 31u;
+    VoxWarp& w = s_w[threadIdx.x >> 5];
+    for (uint32_t s = lane; s < (uint32_t)kVoxSlots; s += 32u)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) w.acc[c][s] = 0.f;
+    __syncwarp();
+    const float A = a.A_f;
+    const uint32_t ndense = *a.ndense;
+    const int TX = 1 << a.ltx, TY = 1 << a.lty, TZ = 1 << a.ltz;
+    const float4 kFar = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);  // never within reach of a target
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&a.nsparse[1], 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= ndense) break;
+        const uint32_t tile = a.tlist[it];
+        const int r = rep_of_tile(a.grids, a.nrep, tile);
+        const GridDev& g = a.grids[r];
+        const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+        const uint32_t lt = tile - g.tbase;
+        const uint32_t rest = lt / (uint32_t)g.nt[0];
+        const int x0 = (int)(lt % (uint32_t)g.nt[0]) * TX;
+        const int y0 = (int)(rest % (uint32_t)g.nt[1]) * TY;
+        const int z0 = (int)(rest / (uint32_t)g.nt[1]) * TZ;
+        const int x1 = min(x0 + TX, n0), y1 = min(y0 + TY, n1), z1 = min(z0 + TZ, n2);
+        const float cut0 = g.qm + a.cut_eps;
+        uint32_t qn = 0, nslot = 0;
+        for (int vz = z0; vz < z1; ++vz)
+            for (int vy = y0; vy < y1; ++vy)
+                for (int vx = x0; vx < x1; ++vx) {
+                    const uint32_t v =
+                        g.vbase + (uint32_t)vx + (uint32_t)n0 * ((uint32_t)vy + (uint32_t)n1 * (uint32_t)vz);
+                    const uint32_t t0 = a.start[v], t1 = a.start[v + 1];
+                    if (t0 == t1) continue;
+                    VoxRuns R;
+                    uint32_t rs = 0, rl = 0;
+                    if (lane < 9u) {
+                        const int jz = vz + (int)(lane / 3u) - 1, jy = vy + (int)(lane % 3u) - 1;
+                        if (jz >= 0 && jz < n2 && jy >= 0 && jy < n1) {
+                            const uint32_t row =
+                                g.vbase + (uint32_t)n0 * ((uint32_t)jy + (uint32_t)n1 * (uint32_t)jz);
+                            rs = a.start[row + (uint32_t)max(vx - 1, 0)];
+                            rl = a.start[row + (uint32_t)min(vx + 2, n0)] - rs;
+                        }
+                    }
+                    uint32_t incl = rl;
+#pragma unroll
+                    for (int o = 1; o < 16; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= (uint32_t)o) incl += y;
+                    }
+                    R.L = __shfl_sync(0xFFFFFFFFu, incl, 8);
+                    R.off = incl - rl;
+                    R.len = rl;
+                    {
+                        const uint32_t nem = __ballot_sync(0xFFFFFFFFu, rl != 0u);
+                        __syncwarp();
+                        if (rl != 0u) w.rdel[__popc(nem & lanemask_lt())] = rs - R.off;
+                        __syncwarp();
+                    }
+                    const uint32_t nch = (R.L + 31u) >> 5;
+                    // the first chunks stay in registers; later ones are reloaded per target
+                    float4 cr[kVoxCached];
+                    uint32_t cjj[kVoxCached];
+#pragma unroll
+                    for (int k = 0; k < kVoxCached; ++k) {
+                        cjj[k] = 0xFFFFFFFFu;
+                        cr[k] = kFar;
+                        if ((uint32_t)k < nch) {
+                            const uint32_t j = vox_cand_index(w, R, 32u * (uint32_t)k);
+                            if (32u * (uint32_t)k + lane < R.L) {
+                                cjj[k] = j;
+                                cr[k] = __ldg(&a.B.rec[2 * (size_t)j]);
+                            }
+                        }
+                    }
+                    for (uint32_t tb = t0; tb < t1;) {
+                        const uint32_t take = min(t1 - tb, (uint32_t)kVoxSlots - nslot);
+                        if (take == 0) {
+                            vox_close<MODE>(a, g, w, qn, nslot);
+                            continue;
+                        }
+                        for (uint32_t k = lane; k < take; k += 32u) w.tq[nslot + k] = tb + k;
+                        __syncwarp();
+                        for (uint32_t k = 0; k < take; ++k) {
+                            const uint32_t q = tb + k;
+                            const uint32_t slot = nslot + k;
+                            const float4 pi = __ldg(&a.B.rec[2 * (size_t)q]);
+                            const float cut_i = fmaf(A, pi.w, cut0);
+                            // test: append the hits of one chunk to the queue (candidate order)
+                            auto test = [&](const float4& c4, uint32_t j) {
+                                const bool hit = j != q && candidate_hit(pi.x - c4.x, pi.y - c4.y, pi.z - c4.z, A,
+                                                                         c4.w, cut_i);
+                                const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+                                if (hit) {
+                                    const uint32_t pos = qn + (uint32_t)__popc(m & lanemask_lt());
+                                    w.qj[pos] = j;
+                                    w.qs[pos] = (uint8_t)slot;
+                                }
+                                qn += (uint32_t)__popc(m);
+                            };
+#pragma unroll
+                            for (int ch = 0; ch < kVoxCached; ++ch)
+                                if ((uint32_t)ch < nch) test(cr[ch], cjj[ch]);
+                            while (qn >= 32u) vox_flush(a, g, w, qn);
+                            for (uint32_t ch = kVoxCached; ch < nch; ++ch) {
+                                const uint32_t j = vox_cand_index(w, R, 32u * ch);
+                                const bool in = 32u * ch + lane < R.L;
+                                test(in ? __ldg(&a.B.rec[2 * (size_t)j]) : kFar, in ? j : 0xFFFFFFFFu);
+                                if (qn >= 32u) vox_flush(a, g, w, qn);
+                            }
+                        }
+                        nslot += take;
+                        tb += take;
+                    }
+                }
+        vox_close<MODE>(a, g, w, qn, nslot);
     }
 }
 
@@ -909,6 +1195,12 @@ cudaError_t launch_tile_mode(const StepArgs& a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int MODE>
+cudaError_t launch_vox_mode(const StepArgs& a, int grid, cudaStream_t s) {
+    k_force_vox<MODE><<<grid, kVoxWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LX, int LZ>
 int tile_grid_for(int sms) {
     using C = TileCfg<LX, LZ>;
@@ -944,6 +1236,11 @@ int force_max_blocks_per_sm(int mode, int block) {
 }
 
 int tile_kernel_grid(const StepArgs& a, int sms) {
+    if (a.tile_kernel == kTileKernelVox) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_vox<kMixedKahan>, kVoxWarps * 32, 0);
+        return sms * (nb > 0 ? nb : 1);
+    }
     if (a.ltx == 3) return tile_grid_for<3, 2>(sms);
     return a.ltz == 3 ? tile_grid_for<2, 3>(sms) : tile_grid_for<2, 2>(sms);
 }
@@ -958,6 +1255,9 @@ cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
 
 cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
+    if (a.tile_kernel == kTileKernelVox)
+        return a.mode == kMixedFP64Pos ? launch_vox_mode<kMixedFP64Pos>(a, grid, s)
+                                       : launch_vox_mode<kMixedKahan>(a, grid, s);
     if (a.mode == kMixedFP64Pos) return launch_tile_shape<kMixedFP64Pos>(a, grid, s);
     return launch_tile_shape<kMixedKahan>(a, grid, s);
 }

@@ -60,6 +60,11 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;  // voxels per scan block
 
+// Dense-tile force kernels: one warp per voxel of a dense tile (any tile), or
+// one block per interior tile with its halo staged in shared memory.
+constexpr int kTileKernelVox = 0;
+constexpr int kTileKernelCTA = 1;
+
 // Device error flag bits (the host reports any of them as MECH_E_DEVICE_FLAG).
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrIndex = 2u;
@@ -164,7 +169,8 @@ struct StepArgs {
     uint32_t* err;
     // tiles
     int ltx, lty, ltz;     // log2 of the tile dimensions (voxels)
-    int use_tiles;         // 1: dense tiles go to the shared-memory tile kernel
+    int use_tiles;         // 1: dense tiles go to a dense-tile kernel
+    int tile_kernel;       // kTileKernelVox (warp per voxel) or kTileKernelCTA (block per interior tile)
     uint32_t ntiles;       // tiles over all replicates
     uint32_t dense_min;    // a tile with at least this many cells is dense
     uint32_t* tcount_cur;

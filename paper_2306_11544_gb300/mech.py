@@ -33,6 +33,10 @@ MECH_E_STATE = -8
 MECH_FP64 = 0
 MECH_MIXED_FP64POS = 1
 MECH_MIXED_KAHAN = 2
+
+MECH_DENSE_WARP_PER_VOXEL = 0
+MECH_DENSE_BLOCK_PER_TILE = 1
+DENSE_KERNELS = {"warp_per_voxel": MECH_DENSE_WARP_PER_VOXEL, "block_per_tile": MECH_DENSE_BLOCK_PER_TILE}
 MODES = {"fp64": MECH_FP64, "mixed": MECH_MIXED_FP64POS, "fp64pos": MECH_MIXED_FP64POS,
          "kahan": MECH_MIXED_KAHAN}
 
@@ -40,7 +44,7 @@ MODES = {"fp64": MECH_FP64, "mixed": MECH_MIXED_FP64POS, "fp64pos": MECH_MIXED_F
 EXPORTS = [
     "mech_last_error", "mech_version", "mech_create", "mech_create_batch", "mech_set_params",
     "mech_set_domain", "mech_set_precision", "mech_set_internal_voxel", "mech_set_launch",
-    "mech_set_tiling", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
+    "mech_set_tiling", "mech_set_dense_kernel", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
     "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_add_cells_batch", "mech_debug_bins",
@@ -98,6 +102,7 @@ def load_library(path: str = LIB_PATH):
             "mech_set_internal_voxel": ([_P, ctypes.c_double], ctypes.c_int),
             "mech_set_launch": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_set_tiling": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+            "mech_set_dense_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_set_stream": ([_P, _P], ctypes.c_int),
             "mech_set_graph": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_step": ([_P, ctypes.c_int64], ctypes.c_int),
@@ -249,6 +254,11 @@ def mech_set_launch(h, force_block):
 def mech_set_tiling(h, tile=(4, 4, 4), dense_min=12):
     tx, ty, tz = (0, 0, 0) if tile is None else tile
     _check(load_library().mech_set_tiling(h, int(tx), int(ty), int(tz), int(dense_min)), "mech_set_tiling")
+
+
+def mech_set_dense_kernel(h, kernel):
+    k = DENSE_KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(load_library().mech_set_dense_kernel(h, k), "mech_set_dense_kernel")
 
 
 def mech_set_stream(h, stream):
@@ -437,6 +447,9 @@ class Mech:
 
     def set_tiling(self, tile=(4, 4, 4), dense_min=12):
         mech_set_tiling(self.h, tile, dense_min)
+
+    def set_dense_kernel(self, kernel):
+        mech_set_dense_kernel(self.h, kernel)
 
     def set_stream(self, stream):
         mech_set_stream(self.h, stream)

@@ -15,6 +15,7 @@ from tests import gpu_helpers as H
 pytestmark = pytest.mark.gpu
 
 MODES = ["fp64", "mixed", "kahan"]
+DENSE_KERNELS = ["warp_per_voxel", "block_per_tile"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -259,17 +260,21 @@ def test_nonfinite_state_raises_device_flag():
         assert e.value.code == mech.MECH_E_DEVICE_FLAG
 
 
+@pytest.mark.parametrize("kernel", DENSE_KERNELS)
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
 @pytest.mark.parametrize("tiling", [None, ((4, 4, 4), 32), ((4, 4, 4), 1), ((4, 4, 8), 32), ((4, 4, 8), 1),
                                     ((8, 4, 4), 32), ((8, 4, 4), 1)],
                          ids=["cells_only", "t444", "t444_all_dense", "t448", "t448_all_dense", "t844",
                               "t844_all_dense"])
-def test_tiled_force_matches_oracle(mode, tiling):
-    """The shared-memory tile kernel (dense tiles) and the thread-per-cell
-    kernel (the rest) give the same velocities as the oracle, for every tile
-    shape and density threshold, including every tile treated as dense."""
+def test_tiled_force_matches_oracle(mode, tiling, kernel):
+    """Either dense-tile kernel (warp per voxel, or block per tile with the
+    halo in shared memory) and the thread-per-cell kernel (the rest) give the
+    same velocities as the oracle, for every tile shape and density
+    threshold, including every tile treated as dense (the warp-per-voxel
+    kernel then also takes the tiles at the grid faces)."""
     pop = synth.clustered_20m(seed=9, scale=0.002)
     with H.make(pop, mode) as m:
+        m.set_dense_kernel(kernel)
         m.set_tiling(*tiling) if tiling else m.set_tiling(None)
         for _ in range(2):
             x = m.positions()
@@ -280,25 +285,31 @@ def test_tiled_force_matches_oracle(mode, tiling):
         check_bins(m, pop, mode)
 
 
+@pytest.mark.parametrize("kernel", DENSE_KERNELS)
 @pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
-def test_tile_halo_overflow_falls_back(mode, tile):
-    """A crowd whose tile halo exceeds the shared-memory capacity is handed
-    back to the thread-per-cell kernel."""
+def test_tile_halo_overflow_falls_back(mode, tile, kernel):
+    """A crowd far denser than a tissue (3,000 cells in two voxels' width):
+    the block-per-tile kernel's halo exceeds its shared-memory capacity and
+    the tile is handed back to the thread-per-cell kernel; the warp-per-voxel
+    kernel takes it with more than 64 targets per voxel and more candidates
+    than its registers hold (the reloading path)."""
     rng = np.random.Generator(np.random.PCG64(31))
     xyz = rng.uniform(250.0, 305.0, size=(3000, 3))  # inside an interior tile of either shape
     pop = H.tiny_population(xyz, [0] * 3, [720] * 3)
     with H.make(pop, mode) as m:
+        m.set_dense_kernel(kernel)
         m.set_tiling(tile, 32)
         v = m.compute_velocities()
     vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
     assert H.rel_err(v, vref) <= H.TOL_V_MIXED
 
 
+@pytest.mark.parametrize("kernel", DENSE_KERNELS)
 @pytest.mark.parametrize("radii", ["uniform", "spread"])
 @pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
-def test_tile_scan_keeps_pairs_at_the_cutoff(mode, tile, radii):
+def test_tile_scan_keeps_pairs_at_the_cutoff(mode, tile, radii, kernel):
     """Every interacting pair of a jittered cubic lattice (13,824 cells, every
     tile dense) sits just inside the adhesion cutoff, 1 - d/(A S) between
     6e-4 and 5.4e-3, and all diagonal pairs are out of range: each velocity is
@@ -320,6 +331,7 @@ def test_tile_scan_keeps_pairs_at_the_cutoff(mode, tile, radii):
     pop = H.tiny_population(xyz, [-300] * 3, [300] * 3, R=R)
     hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
     with H.make(pop, mode, voxel=hmin) as m:
+        m.set_dense_kernel(kernel)
         m.set_tiling(tile, 1)
         v = m.compute_velocities()
     vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
@@ -437,8 +449,9 @@ def test_pair_stats_match_oracle(name, voxel, mode):
     assert pairs > 0 and cand > 2 * pairs
 
 
-@pytest.mark.parametrize("tile", [(4, 4, 8), (8, 4, 4)])
-def test_runs_are_bitwise_reproducible(tile):
+@pytest.mark.parametrize("kernel", DENSE_KERNELS)
+@pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
+def test_runs_are_bitwise_reproducible(tile, kernel):
     """The slot order the scatter takes from atomics never reaches the result:
     two handles advanced the same way end bitwise equal (dense tiles, sparse
     cells and hand-back paths all active)."""
@@ -447,6 +460,7 @@ def test_runs_are_bitwise_reproducible(tile):
     xs = []
     for _ in range(2):
         with H.make(pop, "kahan", voxel=hmin) as m:
+            m.set_dense_kernel(kernel)
             m.set_tiling(tile, 16)
             m.step(12)
             xs.append(m.read_state())
