@@ -76,7 +76,7 @@ def parse():
     p.add_argument("--tile", default="4,4,4",
                    help="voxel tile for dense regions (4,4,4, 4,4,8 or 8,4,4), or 0 for none")
     p.add_argument("--dense-min", type=int, default=12)
-    p.add_argument("--dense-kernel", default="warp_per_voxel", choices=["warp_per_voxel", "block_per_tile"],
+    p.add_argument("--dense-kernel", default="block_per_tile", choices=["block_per_tile", "warp_per_voxel"],
                    help="kernel for the cells of dense tiles")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")

@@ -147,12 +147,12 @@ MECH_API int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t 
  * Kernel for the cells of dense tiles (autotuner knob; no counterpart in the
  * paper, whose update-velocity loop is one thread per cell or per voxel of an
  * OpenMP team, Sec. 5.4):
- *   MECH_DENSE_WARP_PER_VOXEL (default): 32 threads per voxel - the lanes hold
- *     the voxel's candidates and its target cells are taken in turn; works on
- *     any dense tile;
- *   MECH_DENSE_BLOCK_PER_TILE: one thread per target cell, the tile's halo
- *     staged in shared memory by TMA bulk copies; interior tiles only (tiles
- *     touching a grid face go to the thread-per-cell kernel).
+ *   MECH_DENSE_BLOCK_PER_TILE (default): one thread per target cell, the
+ *     tile's halo staged in shared memory by TMA bulk copies; interior tiles
+ *     only (tiles touching a grid face go to the thread-per-cell kernel);
+ *   MECH_DENSE_WARP_PER_VOXEL: 32 threads per voxel - the lanes hold the
+ *     voxel's candidates and its target cells are taken in turn; works on any
+ *     dense tile.
  * Both give velocities within FP32 rounding of each other (their summation
  * orders differ); each is bitwise reproducible run to run.
  */

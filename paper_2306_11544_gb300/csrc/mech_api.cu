@@ -74,7 +74,7 @@ struct mech {
     // voxel tiles
     int ltx = 2, lty = 2, ltz = 2;
     bool use_tiles = true;
-    int tile_kernel = kTileKernelVox;
+    int tile_kernel = kTileKernelCTA;
     uint32_t dense_min = 12;
     uint32_t NT = 0;
     size_t tcap = 0;
