@@ -8,7 +8,8 @@ shares no code with it.
 
 The C file holds the definition (binning by stable counting sort, the
 neighbour-gather repulsion/adhesion velocity of the paper's "update velocity"
-region, Sec. 5.4, and two-step Adams-Bashforth integration); the second the
+region, Sec. 5.4, and two-step Adams-Bashforth integration, with the per-type
+adhesion affinity and domain-wall variants of that region); the second the
 diffusion-decay step (three one-dimensional implicit solves, no-flux faces)
 and the gradients of the microenvironment regions of Sec. 5.1-5.2.  This module
 only compiles them and marshals numpy arrays; it adds no arithmetic of its own.
@@ -88,6 +89,14 @@ class OracleLib:
         lib.oracle_ab2.argtypes = [_I64, _P, _P, _P, _D]
         lib.oracle_run.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _I64, _P]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_velocities_ext.argtypes = [_I64, _P, _P, _P, _P, _D, _P, _D, _P, ctypes.c_int32, _P, _P,
+                                              ctypes.c_int32, _P, _P, _D, _P]
+        lib.oracle_velocities_ext.restype = ctypes.c_int
+        lib.oracle_velocities_allpairs_ext.argtypes = [_I64, _P, _P, _P, _P, _D, ctypes.c_int32, _P, _P,
+                                                       ctypes.c_int32, _P, _P, _D, _P]
+        lib.oracle_run_ext.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _P, _D, _P, ctypes.c_int32, _P, _P,
+                                       ctypes.c_int32, _P, _P, _D, _D, _I64, _P]
+        lib.oracle_run_ext.restype = ctypes.c_int
         if hasattr(lib, "oracle_diffusion_step"):  # absent from single-file test variants
             lib.oracle_diffusion_step.argtypes = [_I64, _I64, _I64, ctypes.c_int32, _P, _P, _P, _D, _D, _I64]
             lib.oracle_diffusion_step.restype = ctypes.c_int
@@ -210,6 +219,66 @@ class OracleLib:
         return xyz, vprev, v
 
 
+    @staticmethod
+    def _variant(n, types, aff, walls):
+        """Marshal the variant arguments: types (n ints in [0, T)), aff (T x T,
+        None = no affinity: T = 1, all ones), walls (None or (wlo, whi, mask,
+        c_w))."""
+        if aff is None:
+            aff = np.ones((1, 1))
+            types = np.zeros(n, dtype=np.int32)
+        aff = _f64(aff).reshape(aff.shape[0] if hasattr(aff, "shape") else len(aff), -1)
+        T = aff.shape[0]
+        types = np.ascontiguousarray(types, dtype=np.int32).reshape(n)
+        if n and (types.min() < 0 or types.max() >= T):
+            raise ValueError("cell types outside [0, T)")
+        if walls is None:
+            wlo, whi, mask, cw = np.zeros(3), np.zeros(3), 0, 0.0
+        else:
+            wlo, whi, mask, cw = walls
+        wlo = _f64(wlo, 3)
+        whi = _f64(whi, 3)
+        return T, types, np.ascontiguousarray(aff), wlo, whi, int(mask), float(cw)
+
+    def velocities_ext(self, xyz, R, ccr, cca, A, lo, h, dims, types=None, aff=None, walls=None):
+        xyz = _f64(xyz).reshape(-1, 3)
+        n = xyz.shape[0]
+        R, ccr, cca = _f64(R, n), _f64(ccr, n), _f64(cca, n)
+        lo, dims = _grid(lo, dims)
+        T, types, aff, wlo, whi, mask, cw = self._variant(n, types, aff, walls)
+        v = np.empty((n, 3), dtype=np.float64)
+        if self.lib.oracle_velocities_ext(n, _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), float(A), _ptr(lo),
+                                          float(h), _ptr(dims), T, _ptr(types), _ptr(aff), mask, _ptr(wlo),
+                                          _ptr(whi), cw, _ptr(v)) != 0:
+            raise MemoryError("oracle_velocities_ext: allocation failed")
+        return v
+
+    def velocities_allpairs_ext(self, xyz, R, ccr, cca, A, types=None, aff=None, walls=None):
+        xyz = _f64(xyz).reshape(-1, 3)
+        n = xyz.shape[0]
+        R, ccr, cca = _f64(R, n), _f64(ccr, n), _f64(cca, n)
+        T, types, aff, wlo, whi, mask, cw = self._variant(n, types, aff, walls)
+        v = np.empty((n, 3), dtype=np.float64)
+        self.lib.oracle_velocities_allpairs_ext(n, _ptr(xyz), _ptr(R), _ptr(ccr), _ptr(cca), float(A), T,
+                                                _ptr(types), _ptr(aff), mask, _ptr(wlo), _ptr(whi), cw, _ptr(v))
+        return v
+
+    def run_ext(self, xyz, R, ccr, cca, A, lo, h, dims, dt, steps, types=None, aff=None, walls=None,
+                vprev=None):
+        """Advance `steps` steps with the variants.  Returns (xyz, vprev, v_last)."""
+        xyz = _f64(xyz).reshape(-1, 3).copy()
+        n = xyz.shape[0]
+        R, ccr, cca = _f64(R, n), _f64(ccr, n), _f64(cca, n)
+        vprev = np.zeros((n, 3)) if vprev is None else _f64(vprev).reshape(-1, 3).copy()
+        v = np.zeros((n, 3), dtype=np.float64)
+        lo, dims = _grid(lo, dims)
+        T, types, aff, wlo, whi, mask, cw = self._variant(n, types, aff, walls)
+        if self.lib.oracle_run_ext(n, _ptr(xyz), _ptr(vprev), _ptr(R), _ptr(ccr), _ptr(cca), float(A), _ptr(lo),
+                                   float(h), _ptr(dims), T, _ptr(types), _ptr(aff), mask, _ptr(wlo), _ptr(whi),
+                                   cw, float(dt), int(steps), _ptr(v)) != 0:
+            raise MemoryError("oracle_run_ext: allocation failed")
+        return xyz, vprev, v
+
     def diffusion_step(self, rho, D, lam, dx, dt, steps):
         """rho: (S, nz, ny, nx) densities, advanced `steps` steps (a copy is returned)."""
         rho = _f64(rho).copy()
@@ -297,6 +366,18 @@ def ab2(xyz, v, vprev, dt):
 
 def run(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, vprev=None):
     return _load().run(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, vprev)
+
+
+def velocities_ext(xyz, R, ccr, cca, A, lo, h, dims, types=None, aff=None, walls=None):
+    return _load().velocities_ext(xyz, R, ccr, cca, A, lo, h, dims, types, aff, walls)
+
+
+def velocities_allpairs_ext(xyz, R, ccr, cca, A, types=None, aff=None, walls=None):
+    return _load().velocities_allpairs_ext(xyz, R, ccr, cca, A, types, aff, walls)
+
+
+def run_ext(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, types=None, aff=None, walls=None, vprev=None):
+    return _load().run_ext(xyz, R, ccr, cca, A, lo, h, dims, dt, steps, types, aff, walls, vprev)
 
 
 def diffusion_step(rho, D, lam, dx, dt, steps):

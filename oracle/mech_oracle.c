@@ -338,3 +338,164 @@ int oracle_run(int64_t n, double* xyz, double* vprev, const double* R, const dou
     }
     return 0;
 }
+
+/*
+ * Velocity variants (the "update velocity" region with two PhysiCell-style
+ * extensions the paper names the system for but does not state; the
+ * statement is ours):
+ *
+ *   Per-type adhesion affinity.  Every cell carries a type t in [0, T); a
+ *   symmetric T x T matrix a (entries >= 0) scales the adhesion coefficient
+ *   of a pair:  c_a = (a[t_i][t_j] * sqrt(cca_i cca_j)) (1 - d/(A S))^2,
+ *   the product taken in that order.  All entries 1 is the base law.
+ *
+ *   Domain walls.  Each enabled face of the box [wlo, whi] (bit f of `mask`
+ *   for the faces -x, +x, -y, +y, -z, +z, in that order) pushes a cell
+ *   inward when the cell overlaps it: with d_w the distance of the centre
+ *   from the face plane, measured inward (x_d - wlo_d for a low face,
+ *   whi_d - x_d for a high face), and n the inward unit normal,
+ *       t = 1 - d_w / R_i  if 0 < d_w < R_i,   t = 1  if d_w <= 0,
+ *       v_i += c_w t^2 n   (nothing if d_w >= R_i),
+ *   added after the pair terms, face by face in the order above.
+ */
+typedef struct {
+    int32_t ntypes;
+    const int32_t* type;  /* per cell, in [0, ntypes) */
+    const double* aff;    /* ntypes x ntypes, row-major, symmetric */
+    int32_t mask;         /* enabled faces */
+    double wlo[3], whi[3];
+    double cw;            /* wall coefficient (um/min) */
+} variant_t;
+
+/* Pair term with the affinity factor (step 2 of the variant). */
+static void pair_term_aff(const double* xi, const double* xj, double Ri, double Rj, double ccri, double ccrj,
+                          double ccai, double ccaj, double aij, double A, double acc[3]) {
+    double dx = xi[0] - xj[0];
+    double dy = xi[1] - xj[1];
+    double dz = xi[2] - xj[2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    double d = sqrt(d2);
+    if (!(d > 0.0)) return;
+    double S = Ri + Rj;
+    double AS = A * S;
+    if (!(d < AS)) return;
+    double c = 0.0;
+    if (d < S) {
+        double t = 1.0 - d / S;
+        c = sqrt(ccri * ccrj) * (t * t);
+    }
+    double ta = 1.0 - d / AS;
+    c = c - (aij * sqrt(ccai * ccaj)) * (ta * ta);
+    double s = c / d;
+    acc[0] += s * dx;
+    acc[1] += s * dy;
+    acc[2] += s * dz;
+}
+
+/* Wall terms of one cell, added to acc in face order. */
+static void wall_terms(const double* x, double Ri, const variant_t* w, double acc[3]) {
+    for (int f = 0; f < 6; ++f) {
+        if (!(w->mask & (1 << f))) continue;
+        int axis = f / 2;
+        int high = f % 2;
+        double dw = high ? w->whi[axis] - x[axis] : x[axis] - w->wlo[axis];
+        if (!(dw < Ri)) continue;
+        double t = dw > 0.0 ? 1.0 - dw / Ri : 1.0;
+        double push = w->cw * (t * t);
+        acc[axis] += high ? -push : push;
+    }
+}
+
+static double affinity(const variant_t* w, int64_t i, int64_t j) {
+    return w->aff[(int64_t)w->type[i] * w->ntypes + w->type[j]];
+}
+
+static void velocity_one_ext(int64_t i, const bins_t* b, const double* xyz, const double* R, const double* ccr,
+                             const double* cca, double A, const variant_t* w, double out[3]) {
+    const int32_t* n = b->g.n;
+    uint32_t k = b->key[i];
+    int32_t ix = (int32_t)(k % (uint32_t)n[0]);
+    int32_t iy = (int32_t)((k / (uint32_t)n[0]) % (uint32_t)n[1]);
+    int32_t iz = (int32_t)(k / ((uint32_t)n[0] * (uint32_t)n[1]));
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int dz = -1; dz <= 1; ++dz) {
+        int32_t jz = iz + dz;
+        if (jz < 0 || jz >= n[2]) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int32_t jy = iy + dy;
+            if (jy < 0 || jy >= n[1]) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int32_t jx = ix + dx;
+                if (jx < 0 || jx >= n[0]) continue;
+                uint32_t vk = (uint32_t)jx + (uint32_t)n[0] * ((uint32_t)jy + (uint32_t)n[1] * (uint32_t)jz);
+                for (uint32_t q = b->start[vk]; q < b->start[vk + 1]; ++q) {
+                    int64_t j = b->order[q];
+                    if (j == i) continue;
+                    pair_term_aff(&xyz[3 * i], &xyz[3 * j], R[i], R[j], ccr[i], ccr[j], cca[i], cca[j],
+                                  affinity(w, i, j), A, acc);
+                }
+            }
+        }
+    }
+    wall_terms(&xyz[3 * i], R[i], w, acc);
+    out[0] = acc[0]; out[1] = acc[1]; out[2] = acc[2];
+}
+
+static void variant_init(variant_t* w, int32_t ntypes, const int32_t* type, const double* aff, int32_t mask,
+                         const double wlo[3], const double whi[3], double cw) {
+    w->ntypes = ntypes;
+    w->type = type;
+    w->aff = aff;
+    w->mask = mask;
+    for (int d = 0; d < 3; ++d) { w->wlo[d] = wlo[d]; w->whi[d] = whi[d]; }
+    w->cw = cw;
+}
+
+/* Step 2 with the variants, binned. */
+int oracle_velocities_ext(int64_t n, const double* xyz, const double* R, const double* ccr, const double* cca,
+                          double A, const double lo[3], double h, const int32_t dims[3], int32_t ntypes,
+                          const int32_t* type, const double* aff, int32_t mask, const double wlo[3],
+                          const double whi[3], double cw, double* v) {
+    variant_t w;
+    variant_init(&w, ntypes, type, aff, mask, wlo, whi, cw);
+    bins_t b;
+    if (bins_build(&b, n, xyz, lo, h, dims) != 0) { bins_free(&b); return -1; }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) velocity_one_ext(i, &b, xyz, R, ccr, cca, A, &w, &v[3 * i]);
+    bins_free(&b);
+    return 0;
+}
+
+/* Step 2 with the variants by all pairs (j ascending), no binning. */
+void oracle_velocities_allpairs_ext(int64_t n, const double* xyz, const double* R, const double* ccr,
+                                    const double* cca, double A, int32_t ntypes, const int32_t* type,
+                                    const double* aff, int32_t mask, const double wlo[3], const double whi[3],
+                                    double cw, double* v) {
+    variant_t w;
+    variant_init(&w, ntypes, type, aff, mask, wlo, whi, cw);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            pair_term_aff(&xyz[3 * i], &xyz[3 * j], R[i], R[j], ccr[i], ccr[j], cca[i], cca[j],
+                          affinity(&w, i, j), A, acc);
+        }
+        wall_terms(&xyz[3 * i], R[i], &w, acc);
+        v[3 * i] = acc[0]; v[3 * i + 1] = acc[1]; v[3 * i + 2] = acc[2];
+    }
+}
+
+/* Full steps 1-3 with the variants (as oracle_run). */
+int oracle_run_ext(int64_t n, double* xyz, double* vprev, const double* R, const double* ccr, const double* cca,
+                   double A, const double lo[3], double h, const int32_t dims[3], int32_t ntypes,
+                   const int32_t* type, const double* aff, int32_t mask, const double wlo[3], const double whi[3],
+                   double cw, double dt, int64_t steps, double* v) {
+    for (int64_t s = 0; s < steps; ++s) {
+        if (oracle_velocities_ext(n, xyz, R, ccr, cca, A, lo, h, dims, ntypes, type, aff, mask, wlo, whi, cw,
+                                  v) != 0)
+            return -1;
+        oracle_ab2(n, xyz, v, vprev, dt);
+    }
+    return 0;
+}
