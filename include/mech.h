@@ -7,9 +7,12 @@
  * the non-empty-voxel variant that follows it), plus the position update.
  *
  * One step (mech_step) does, for every cell i:
- *   1. Binning.  i_d = clamp(floor((x_d - lo_d) / h), 0, n_d - 1) on a uniform
+ *   1. Binning.  i_d = clamp(floor((x_d - lo_d) * (1/h)), 0, n_d - 1) on a uniform
  *      voxel grid of side h over the domain [lo, hi] (n_d = ceil((hi_d -
- *      lo_d) / h)); cells outside the domain are counted in the edge voxel;
+ *      lo_d) / h); the index is one IEEE subtraction and one multiplication
+ *      by the once-rounded reciprocal 1/h, no contraction, in the precision
+ *      of the positions); cells outside the domain are counted in the edge
+ *      voxel;
  *      the cells are then permuted into voxel order by a counting sort
  *      (histogram, exclusive scan, scatter) whose order inside a voxel is
  *      ascending caller index.  This is the GPU form of the paper's lesson
@@ -24,6 +27,9 @@
  *      v_i,prev = v_i.  Before the first step v_prev = 0.
  * The paper names these regions but prints none of the formulas; the force
  * law and the integrator above are the problem this library solves.
+ *
+ * Optional velocity variants (mech_set_affinity, mech_set_walls): a per-type
+ * adhesion affinity that scales c_a, and repulsive domain walls.
  *
  * Beyond the step: cells removed and added between steps (mech_remove_cells,
  * mech_add_cells, mech_add_cells_batch), and a substrate diffusion solver
@@ -84,7 +90,8 @@ MECH_API int mech_version(void);
 /*
  * Create a handle for one population of n >= 0 cells on the current CUDA
  * device.  xyz: 3n doubles; R (radius, > 0), ccr, cca (>= 0): n doubles each;
- * type: n int32 (carried, unused by the force; may be NULL).  The arrays are
+ * type: n int32 cell types in [0, 16) (used only by the per-type adhesion
+ * affinity, mech_set_affinity; NULL = all type 0).  The arrays are
  * copied.  Precision defaults to MECH_MIXED_FP64POS; parameters must be set
  * with mech_set_params before the first step.  The domain defaults to a cube
  * centred at the origin whose half side is 1.5 times the largest |coordinate|
@@ -159,6 +166,32 @@ MECH_API int mech_set_tiling(mech_t* h, int32_t tile_x, int32_t tile_y, int32_t 
 #define MECH_DENSE_WARP_PER_VOXEL 0
 #define MECH_DENSE_BLOCK_PER_TILE 1
 MECH_API int mech_set_dense_kernel(mech_t* h, int32_t kernel);
+
+/*
+ * Per-type adhesion affinity (a velocity variant; the paper names PhysiCell,
+ * Sec. 3.2, whose cell types adhere selectively, but states no law; the
+ * statement is this library's): aff is an ntypes x ntypes row-major matrix,
+ * symmetric, finite entries >= 0, ntypes in [1, 16] and above every cell's
+ * type.  The adhesion coefficient of a pair becomes
+ *   c_a = (aff[t_i][t_j] sqrt(cca_i cca_j)) (1 - d/(A S))^2.
+ * ntypes = 0 or aff = NULL switches the affinity off (the base law; a matrix
+ * of ones gives the same velocities).  The library copies the matrix.
+ * Errors: MECH_E_ARG (size, sign, asymmetry, a cell type outside the table),
+ * MECH_E_NONFINITE.
+ */
+MECH_API int mech_set_affinity(mech_t* h, int32_t ntypes, const double* aff);
+
+/*
+ * Domain walls (a velocity variant; statement as for the affinity): bit f of
+ * face_mask enables face f of every replicate's domain box (mech_set_domain),
+ * in the order -x, +x, -y, +y, -z, +z.  A cell whose centre lies at inward
+ * distance d_w from an enabled face, d_w < R_i, is pushed along the inward
+ * normal by c_wall t^2, t = 1 - d_w / R_i for d_w > 0 and t = 1 at or beyond
+ * the face; the terms are added after the pair terms, face by face in the
+ * order above.  face_mask = 0 switches the walls off.  c_wall in um/min,
+ * finite and >= 0.  Errors: MECH_E_ARG, MECH_E_NONFINITE.
+ */
+MECH_API int mech_set_walls(mech_t* h, int32_t face_mask, double c_wall);
 
 /* Stream (a cudaStream_t) for all device work of this handle; NULL = the
  * handle's own stream.  The caller keeps the stream alive. */

@@ -74,6 +74,13 @@ struct mech {
     // voxel tiles
     int ltx = 2, lty = 2, ltz = 2;
     bool use_tiles = true;
+    // velocity variants
+    int32_t max_type = -1;         // largest cell type created or added so far
+    int32_t ntypes = 0;            // > 0: affinity table in use
+    float* d_aff_f = nullptr;      // 16 x 16 affinity tables (FP32, FP64)
+    double* d_aff_d = nullptr;
+    int32_t walls = 0;
+    double c_wall = 0.0;
     int tile_kernel = kTileKernelCTA;
     uint32_t dense_min = 12;
     uint32_t NT = 0;
@@ -215,6 +222,11 @@ struct mech {
         a.lty = lty;
         a.ltz = ltz;
         a.use_tiles = use_tiles ? 1 : 0;
+        a.ntypes = ntypes;
+        a.aff_f = d_aff_f;
+        a.aff_d = d_aff_d;
+        a.walls = walls;
+        a.c_wall = c_wall;
         a.tile_kernel = tile_kernel;
         a.ntiles = NT;
         a.dense_min = dense_min;
@@ -263,6 +275,10 @@ int build_grids(mech_t* h) {
             G.n[d] = (int32_t)nd;
             G.lo[d] = lo[d];
             G.lo_f[d] = (float)lo[d];
+        }
+        for (int d = 0; d < 3; ++d) {
+            G.whi[d] = hi[d];
+            G.whi_f[d] = (float)hi[d];
         }
         G.h = vx;
         G.inv_h = 1.0 / vx;
@@ -627,14 +643,31 @@ int set_cell_counts(mech_t* h, const std::vector<int64_t>& counts) {
     return MECH_OK;
 }
 
+// Cell types must lie in [0, 16) (they travel in 4 bits of the force
+// record); returns the largest one (-1 for none).
+int check_types(int64_t n, const int32_t* type, int32_t& max_type) {
+    max_type = -1;
+    if (!type) {
+        if (n > 0) max_type = 0;
+        return MECH_OK;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (type[i] < 0 || type[i] >= kMaxTypes) return fail(MECH_E_ARG, "cell types must lie in [0, 16)");
+        max_type = std::max(max_type, type[i]);
+    }
+    return MECH_OK;
+}
+
 int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double* xyz, const double* R,
-                const double* ccr, const double* cca) {
+                const double* ccr, const double* cca, const int32_t* type) {
     int64_t n = 0;
     for (int r = 0; r < nrep; ++r) {
         if (counts[r] < 0) return fail(MECH_E_ARG, "negative replicate count");
         n += counts[r];
     }
     MECH_TRY(validate_cells(n, xyz, R, ccr, cca));
+    int32_t max_type = -1;
+    MECH_TRY(check_types(n, type, max_type));
     mech_t* h = new (std::nothrow) mech_t();
     if (!h) return fail(MECH_E_OOM, "host allocation failed");
     auto bail = [&](int rc) {
@@ -652,6 +685,7 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     h->stream = h->own_stream;
     h->n = n;
     h->nrep = nrep;
+    h->max_type = max_type;
     h->npad = (uint32_t)((n + 63) / 64 * 64);
     if (h->npad == 0) h->npad = 64;
     h->counts.assign(counts, counts + nrep);
@@ -682,14 +716,11 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
     std::vector<float4> rec(2 * n);
     for (int64_t i = 0; i < n; ++i) {
         ids[i] = (uint32_t)i;
-        // radius as FP32 + 16-bit residual in units of ulp(R) / 2^15 (upper half
-        // of the second float4); position residual fields start at zero (0x8000)
+        // radius as FP32 + 12-bit residual in units of ulp(R) / 2^11 and the
+        // type (upper half of the second float4); position residual fields
+        // start at zero (0x8000)
         const float Rf = (float)R[i];
-        int e2 = 0;
-        std::frexp(Rf, &e2);  // Rf = m 2^e2, m in [0.5, 1): ulp = 2^(e2 - 24)
-        const double units = (R[i] - (double)Rf) / std::ldexp(1.0, e2 - 24);
-        const long L = std::lround(std::min(32767.0, std::max(-32768.0, units * 32768.0)));
-        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
+        const uint32_t wzr = 0x8000u | radius_type_bits(R[i], Rf, type ? (uint32_t)type[i] : 0u);
         float wzf, wxyf;
         const uint32_t wxy = 0x80008000u;
         std::memcpy(&wzf, &wzr, 4);
@@ -748,19 +779,17 @@ int mech_version(void) { return 100; }
 
 int mech_create(mech_t** h, int64_t n, const double* xyz, const double* R, const double* ccr, const double* cca,
                 const int32_t* type) {
-    (void)type;
     if (!h) return fail(MECH_E_ARG, "null output handle pointer");
     *h = nullptr;
-    return create_impl(h, 1, &n, xyz, R, ccr, cca);
+    return create_impl(h, 1, &n, xyz, R, ccr, cca, type);
 }
 
 int mech_create_batch(mech_t** h, int32_t n_rep, const int64_t* counts, const double* xyz, const double* R,
                       const double* ccr, const double* cca, const int32_t* type) {
-    (void)type;
     if (!h) return fail(MECH_E_ARG, "null output handle pointer");
     *h = nullptr;
     if (n_rep < 1 || !counts) return fail(MECH_E_ARG, "n_rep must be >= 1 with a counts array");
-    return create_impl(h, n_rep, counts, xyz, R, ccr, cca);
+    return create_impl(h, n_rep, counts, xyz, R, ccr, cca, type);
 }
 
 int mech_set_params(mech_t* h, double A, double voxel_size, double dt) {
@@ -858,6 +887,54 @@ int mech_set_dense_kernel(mech_t* h, int32_t kernel) {
         h->tile_grid = tile_kernel_grid(h->args(0, 1), h->sms);
         h->invalidate_graphs();
     }
+    return MECH_OK;
+}
+
+int mech_set_affinity(mech_t* h, int32_t ntypes, const double* aff) {
+    MECH_TRY(check_handle(h));
+    if (ntypes == 0 || !aff) {
+        h->ntypes = 0;
+        h->invalidate_graphs();
+        return MECH_OK;
+    }
+    if (ntypes < 1 || ntypes > kMaxTypes) return fail(MECH_E_ARG, "ntypes must lie in [1, 16]");
+    if (h->max_type >= ntypes)
+        return fail(MECH_E_ARG, "a cell's type (" + std::to_string(h->max_type) + ") is outside the table");
+    float tf[kMaxTypes * kMaxTypes];
+    double td[kMaxTypes * kMaxTypes];
+    for (int i = 0; i < kMaxTypes * kMaxTypes; ++i) {
+        tf[i] = 1.0f;
+        td[i] = 1.0;
+    }
+    for (int i = 0; i < ntypes; ++i)
+        for (int j = 0; j < ntypes; ++j) {
+            const double v = aff[i * ntypes + j];
+            if (!std::isfinite(v)) return fail(MECH_E_NONFINITE, "non-finite affinity");
+            if (v < 0.0) return fail(MECH_E_ARG, "affinities must be >= 0");
+            if (v != aff[j * ntypes + i]) return fail(MECH_E_ARG, "the affinity matrix must be symmetric");
+            td[i * kMaxTypes + j] = v;
+            tf[i * kMaxTypes + j] = (float)v;
+        }
+    if (!h->d_aff_f) {
+        MECH_TRY(h->alloc(&h->d_aff_f, (size_t)kMaxTypes * kMaxTypes));
+        MECH_TRY(h->alloc(&h->d_aff_d, (size_t)kMaxTypes * kMaxTypes));
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_aff_f, tf, sizeof(tf), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_aff_d, td, sizeof(td), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host tables die here
+    h->ntypes = ntypes;
+    h->invalidate_graphs();
+    return MECH_OK;
+}
+
+int mech_set_walls(mech_t* h, int32_t face_mask, double c_wall) {
+    MECH_TRY(check_handle(h));
+    if (face_mask < 0 || face_mask > 63) return fail(MECH_E_ARG, "face_mask must lie in [0, 63]");
+    if (!std::isfinite(c_wall)) return fail(MECH_E_NONFINITE, "non-finite wall coefficient");
+    if (c_wall < 0.0) return fail(MECH_E_ARG, "the wall coefficient must be >= 0");
+    h->walls = face_mask;
+    h->c_wall = c_wall;
+    h->invalidate_graphs();
     return MECH_OK;
 }
 
@@ -1148,7 +1225,7 @@ int mech_remove_cells(mech_t* h, const uint8_t* alive) {
 // New cells: per_rep[r] of them for replicate r (all of them for a single
 // population), given in replicate order.
 static int add_cells(mech_t* h, const int64_t* per_rep, int64_t m, const double* xyz, const double* R,
-                     const double* ccr, const double* cca) {
+                     const double* ccr, const double* cca, const int32_t* type) {
     MECH_TRY(check_handle(h));
     if (h->poisoned)
         return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
@@ -1167,6 +1244,10 @@ static int add_cells(mech_t* h, const int64_t* per_rep, int64_t m, const double*
     }
     if (m == 0) return MECH_OK;
     MECH_TRY(validate_cells(m, xyz, R, ccr, cca));
+    int32_t max_type = -1;
+    MECH_TRY(check_types(m, type, max_type));
+    if (h->ntypes > 0 && max_type >= h->ntypes)
+        return fail(MECH_E_ARG, "a new cell's type is outside the affinity table (mech_set_affinity)");
     if (h->n + m >= (int64_t)0x7FFFFFFF) return fail(MECH_E_ARG, "more than 2^31-1 cells");
     double maxR = h->maxR;
     for (int64_t i = 0; i < m; ++i) maxR = std::max(maxR, R[i]);
@@ -1223,30 +1304,33 @@ static int add_cells(mech_t* h, const int64_t* per_rep, int64_t m, const double*
     CUDA_TRY(cudaMemcpyAsync(h->d_io + 4 * m, ccr, m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_io + 5 * m, cca, m * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->d_perm, dst.data(), m * 4, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(launch_append_state(h->args(h->cur, 1), h->st[h->cur], h->d_io, h->d_perm, (uint32_t)m, h->d_R64,
-                                 h->d_ccr64, h->d_cca64, st));
+    // types in the key scratch (the next step recomputes the keys)
+    if (type) CUDA_TRY(cudaMemcpyAsync(h->d_key, type, m * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_append_state(h->args(h->cur, 1), h->st[h->cur], h->d_io, h->d_perm,
+                                 type ? reinterpret_cast<const uint32_t*>(h->d_key) : nullptr,
+                                 (uint32_t)m, h->d_R64, h->d_ccr64, h->d_cca64, st));
     CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above and the caller's arrays are released
     h->maxR = maxR;
+    h->max_type = std::max(h->max_type, max_type);
+    h->keys_valid = false;
     MECH_TRY(set_cell_counts(h, counts2));
     return mech_sync(h);
 }
 
 int mech_add_cells(mech_t* h, int64_t m, const double* xyz, const double* R, const double* ccr, const double* cca,
                    const int32_t* type) {
-    (void)type;
     MECH_TRY(check_handle(h));
     if (h->nrep != 1) return fail(MECH_E_ARG, "mech_add_cells: use mech_add_cells_batch for a batch handle");
-    return add_cells(h, nullptr, m, xyz, R, ccr, cca);
+    return add_cells(h, nullptr, m, xyz, R, ccr, cca, type);
 }
 
 int mech_add_cells_batch(mech_t* h, const int64_t* counts, const double* xyz, const double* R, const double* ccr,
                          const double* cca, const int32_t* type) {
-    (void)type;
     MECH_TRY(check_handle(h));
     if (!counts) return fail(MECH_E_ARG, "null counts");
     int64_t m = 0;
     for (int r = 0; r < h->nrep; ++r) m += counts[r];
-    return add_cells(h, counts, m, xyz, R, ccr, cca);
+    return add_cells(h, counts, m, xyz, R, ccr, cca, type);
 }
 
 int mech_debug_bins(mech_t* h, uint32_t* key, uint32_t* count, uint32_t* start, int64_t* order) {

@@ -473,8 +473,8 @@ __global__ void k_shift_params(const StepArgs a, const uint32_t* __restrict__ sh
 // positions (3 per cell) at io[0, 3m) and their R, ccr, cca at io[3m + k],
 // io[4m + k], io[5m + k].
 __global__ void k_append_state(const StepArgs a, const StateBuf st, const double* __restrict__ io,
-                               const uint32_t* __restrict__ dst, uint32_t m, double* __restrict__ R64,
-                               double* __restrict__ ccr64, double* __restrict__ cca64) {
+                               const uint32_t* __restrict__ dst, const uint32_t* __restrict__ types, uint32_t m,
+                               double* __restrict__ R64, double* __restrict__ ccr64, double* __restrict__ cca64) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const size_t np = a.npad;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
@@ -487,15 +487,11 @@ __global__ void k_append_state(const StepArgs a, const StateBuf st, const double
         R64[q] = R;
         ccr64[q] = ccr;
         cca64[q] = cca;
-        // record: radius as FP32 plus its residual in units of ulp(R) / 2^15
-        // (16 bits, offset 2^15), coefficient square roots; the position
-        // fields are written by the next canonicalisation
+        // record: radius as FP32 plus its residual in units of ulp(R) / 2^11
+        // (12 bits, offset 2^11) and the type, coefficient square roots; the
+        // position fields are written by the next canonicalisation
         const float Rf = __double2float_rn(R);
-        int e2 = 0;
-        frexpf(Rf, &e2);  // Rf = f 2^e2, f in [0.5, 1): ulp(Rf) = 2^(e2 - 24)
-        const double units = (R - (double)Rf) / ldexp(1.0, e2 - 24);
-        const long long L = llround(fmin(32767.0, fmax(-32768.0, units * 32768.0)));
-        const uint32_t wzr = 0x8000u | ((uint32_t)(L + 32768) << 16);
+        const uint32_t wzr = 0x8000u | radius_type_bits(R, Rf, types ? (types[j] & 15u) : 0u);
         st.rec[2 * q] = make_float4(0.f, 0.f, 0.f, Rf);
         st.rec[2 * q + 1] = make_float4(__double2float_rn(sqrt(ccr)), __double2float_rn(sqrt(cca)),
                                         __uint_as_float(0x80008000u), __uint_as_float(wzr));
@@ -600,9 +596,10 @@ cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const
 }
 
 cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, const uint32_t* dst,
-                                uint32_t m, double* R64, double* ccr64, double* cca64, cudaStream_t s) {
+                                const uint32_t* types, uint32_t m, double* R64, double* ccr64, double* cca64,
+                                cudaStream_t s) {
     if (m == 0) return cudaSuccess;
-    k_append_state<<<elementwise_grid(m), 256, 0, s>>>(a, st, io, dst, m, R64, ccr64, cca64);
+    k_append_state<<<elementwise_grid(m), 256, 0, s>>>(a, st, io, dst, types, m, R64, ccr64, cca64);
     return cudaGetLastError();
 }
 

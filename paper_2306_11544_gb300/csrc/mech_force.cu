@@ -154,7 +154,7 @@ struct Acc3 {
 //   A^2 - 1 rounded once.
 __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
                                            float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
-                                           float A, float A2m1, float3& f) {
+                                           float aij, float A, float A2m1, float3& f) {
     const float rx = hx + lx, ry = hy + ly, rz = hz + lz;
     const float d2 = rx * rx + ry * ry + rz * rz;
     float Se;
@@ -177,7 +177,7 @@ __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float l
         const float g = (S2 - D) + (eS - De);
         const float gA = fmaf(S2, A2m1, fmaf(eS, A2m1, g));
         const float ta = __fdividef(gA, AS * (AS + d));
-        float cf = -(sccai * sccaj) * (ta * ta);
+        float cf = -(aij * (sccai * sccaj)) * (ta * ta);
         if (d < S) {
             const float t = __fdividef(g, S * (S + d));
             cf += (sccri * sccrj) * (t * t);
@@ -192,9 +192,10 @@ __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float l
 
 __device__ __forceinline__ void pair_term(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
                                           float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
-                                          float A, float A2m1, Acc3& acc) {
+                                          float aij, float A, float A2m1, Acc3& acc) {
     float3 f;
-    if (pair_force(hx, hy, hz, lx, ly, lz, Ri, Rj, Rlo, sccri, sccai, sccrj, sccaj, A, A2m1, f)) acc.add(f.x, f.y, f.z);
+    if (pair_force(hx, hy, hz, lx, ly, lz, Ri, Rj, Rlo, sccri, sccai, sccrj, sccaj, aij, A, A2m1, f))
+        acc.add(f.x, f.y, f.z);
 }
 
 // Squared candidate cutoff for a target with cut_i = A R_i + margin.
@@ -245,10 +246,24 @@ __device__ __forceinline__ CellState<MODE> load_cell_state(const StepArgs& a, ui
 // in the B order; returns the next step's voxel key and its voxel coordinates.
 template <int MODE>
 __device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& g, uint32_t q,
-                                              const CellState<MODE>& st, float ax, float ay, float az, int& nix,
-                                              int& niy, int& niz) {
+                                              const CellState<MODE>& st, float ax, float ay, float az, float Rf,
+                                              float Rlo, int& nix, int& niy, int& niz) {
     const size_t np = a.npad;
-    const float v[3] = {ax, ay, az};
+    float v[3] = {ax, ay, az};
+    if (a.walls) {  // wall terms (velocity variant): an FP32 test, then FP64 for cells near a face
+        float x0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x0[d] = MODE == kMixedFP64Pos ? __double2float_rn(st.x[d]) : st.xh[d];
+        if (near_wall(a, g, x0, Rf)) {
+            double x[3], w[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                x[d] = MODE == kMixedFP64Pos ? st.x[d] : __dsub_rn((double)st.xh[d], (double)st.cc[d]);
+            wall_terms(a, g, x, __dadd_rn((double)Rf, (double)Rlo), w);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[d] = __fadd_rn(v[d], __double2float_rn(w[d]));
+        }
+    }
     bool finite = true;
     float xf[3];
 #pragma unroll
@@ -287,9 +302,10 @@ __device__ __forceinline__ uint32_t ab2_apply(const StepArgs& a, const GridDev& 
 
 template <int MODE>
 __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDev& g, uint32_t q, uint32_t src,
-                                                 float ax, float ay, float az, int& nix, int& niy, int& niz) {
+                                                 float ax, float ay, float az, float Rf, float Rlo, int& nix,
+                                                 int& niy, int& niz) {
     const CellState<MODE> st = load_cell_state<MODE>(a, src);
-    return ab2_apply<MODE>(a, g, q, st, ax, ay, az, nix, niy, niz);
+    return ab2_apply<MODE>(a, g, q, st, ax, ay, az, Rf, Rlo, nix, niy, niz);
 }
 
 // Next-step histograms (voxels, tiles) and key of cell q; all 32 lanes call it.
@@ -355,7 +371,7 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
                     const float4 qj = a.B.rec[2 * (size_t)j + 1];
                     const float4 lj = record_lo(pj, qj, g.qs);
                     pair_term(hx, hy, hz, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w, li.w + lj.w, qi.x, qi.y,
-                              qj.x, qj.y, A, a.A2m1_f, acc);
+                              qj.x, qj.y, affinity_f(a, record_type(qi), record_type(qj)), A, a.A2m1_f, acc);
                 }
             }
         }
@@ -394,9 +410,11 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(key, g);
             Acc3 acc;
-            velocity_walk(a, g, c, q, alone, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
+            const float4 pq = a.B.rec[2 * (size_t)q], cq = a.B.rec[2 * (size_t)q + 1];
+            velocity_walk(a, g, c, q, alone, pq, cq, acc);
             int nix, niy, niz;
-            nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
+            nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), pq.w, record_lo(pq, cq, g.qs).w, nix,
+                                   niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
         }
         next_step_counts(a, q, nkey, ntile, valid);
@@ -509,7 +527,8 @@ __device__ __noinline__ void vox_flush(const StepArgs& a, const GridDev& g, VoxW
         const float4 li = record_lo(pi, ci, g.qs);
         const float4 lj = record_lo(pj, cj, g.qs);
         pair_force(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w,
-                   li.w + lj.w, ci.x, ci.y, cj.x, cj.y, a.A_f, a.A2m1_f, f);
+                   li.w + lj.w, ci.x, ci.y, cj.x, cj.y, affinity_f(a, record_type(ci), record_type(cj)), a.A_f,
+                   a.A2m1_f, f);
     }
     // segmented suffix sums: slots are non-decreasing over the lanes, so a
     // lane adds the partial sum o lanes up whenever that lane has its slot;
@@ -570,7 +589,13 @@ __device__ __forceinline__ void vox_close(const StepArgs& a, const GridDev& g, V
             const float vy = __fsub_rn(w.acc[1][s], w.acc[4][s]);
             const float vz = __fsub_rn(w.acc[2][s], w.acc[5][s]);
             int nix, niy, niz;
-            nkey = ab2_epilogue<MODE>(a, g, q, a_slot(a, q), vx, vy, vz, nix, niy, niz);
+            float Rf = 0.f, Rlo = 0.f;
+            if (a.walls) {
+                const float4 pq = __ldg(&a.B.rec[2 * (size_t)q]), cq = __ldg(&a.B.rec[2 * (size_t)q + 1]);
+                Rf = pq.w;
+                Rlo = record_lo(pq, cq, g.qs).w;
+            }
+            nkey = ab2_epilogue<MODE>(a, g, q, a_slot(a, q), vx, vy, vz, Rf, Rlo, nix, niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
 #pragma unroll
             for (int c = 0; c < 6; ++c) w.acc[c][s] = 0.f;
@@ -1008,11 +1033,12 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                         const float4 q2 = srec[2 * jj + 1];
                         const float4 l2 = record_lo(p2, q2, g.qs);
                         pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y, li.z - l2.z, pi.w,
-                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, A, a.A2m1_f, acc);
+                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y,
+                                  affinity_f(a, record_type(qi), record_type(q2)), A, a.A2m1_f, acc);
                     }
                 }
                 int nix, niy, niz;
-                nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), nix, niy, niz);
+                nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), pi.w, li.w, nix, niy, niz);
                 ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
             }
             next_step_counts(a, q, nkey, ntile, valid);
@@ -1046,6 +1072,7 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
             const uint32_t idi = a.A.id[src];
             const double xi = a.A.pos64[src], yi = a.A.pos64[np + src], zi = a.A.pos64[2 * np + src];
             const double Ri = a.R64[idi], ccri = a.ccr64[idi], ccai = a.cca64[idi];
+            const uint32_t ti = a.ntypes > 0 ? record_type(a.B.rec[2 * (size_t)q + 1]) : 0u;
             const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int dz = -1; dz <= 1; ++dz) {
@@ -1085,7 +1112,11 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
                                 cf = __dmul_rn(__dsqrt_rn(__dmul_rn(ccri, a.ccr64[idj])), __dmul_rn(t, t));
                             }
                             const double ta = __dsub_rn(1.0, __ddiv_rn(d, AS));
-                            cf = __dsub_rn(cf, __dmul_rn(__dsqrt_rn(__dmul_rn(ccai, a.cca64[idj])), __dmul_rn(ta, ta)));
+                            // adhesion coefficient (a_ij sqrt(cca_i cca_j)); a_ij = 1 without affinity
+                            const double aij =
+                                a.ntypes > 0 ? a.aff_d[ti * kMaxTypes + record_type(a.B.rec[2 * (size_t)j + 1])] : 1.0;
+                            cf = __dsub_rn(cf, __dmul_rn(__dmul_rn(aij, __dsqrt_rn(__dmul_rn(ccai, a.cca64[idj]))),
+                                                         __dmul_rn(ta, ta)));
                             const double sc = __ddiv_rn(cf, d);
                             ax = __dadd_rn(ax, __dmul_rn(sc, dx));
                             ay = __dadd_rn(ay, __dmul_rn(sc, dy2));
@@ -1095,8 +1126,9 @@ __global__ void __launch_bounds__(kCellBlock) k_force_fp64(const StepArgs a) {
                     }
                 }
             }
-            const double v[3] = {ax, ay, az};
+            double v[3] = {ax, ay, az};
             const double xo[3] = {xi, yi, zi};
+            if (a.walls) wall_terms(a, g, xo, Ri, v);  // after the pair terms, as the definition orders them
             double xn[3];
             bool finite = true;
 #pragma unroll

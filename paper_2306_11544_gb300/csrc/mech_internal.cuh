@@ -17,9 +17,11 @@
 //                                 radius (FP32);
 //                                 rec[2i+1] = {sqrt(ccr), sqrt(cca), lo_xy,
 //                                 lo_zr}: the coefficient square roots, then
-//                                 four 16-bit fixed-point residuals: x_lo,
-//                                 y_lo, z_lo in units of q / 2^15 and
-//                                 R - (float)R in units of ulp(R) / 2^15
+//                                 three 16-bit fixed-point residuals x_lo,
+//                                 y_lo, z_lo in units of q / 2^15, then
+//                                 R - (float)R in units of ulp(R) / 2^11
+//                                 (12 bits) and the cell type (4 bits, the
+//                                 top of lo_zr)
 //     The canonicalisation pass writes only the force records in B order;
 //     the force kernels read each cell's state (positions, compensation,
 //     previous velocity) in A order at perm[q] (nearly sequential: cells that
@@ -46,6 +48,7 @@
 // margin of 2q.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 
@@ -62,6 +65,8 @@ constexpr int kScanTile = kScanThreads * kScanItems;  // voxels per scan block
 
 // Dense-tile force kernels: one warp per voxel of a dense tile (any tile), or
 // one block per interior tile with its halo staged in shared memory.
+constexpr int kMaxTypes = 16;  // cell types carried in 4 bits of the force record
+
 constexpr int kTileKernelVox = 0;
 constexpr int kTileKernelCTA = 1;
 
@@ -83,6 +88,8 @@ struct GridDev {
     uint32_t ncell;
     int32_t nt[3];     // tiles per axis
     uint32_t tbase;    // first global tile index of this replicate
+    double whi[3];     // high corner of the domain box (the low corner is lo): the wall planes
+    float whi_f[3];    // (float)whi
     double oc[3];      // grid centre: origin of the record positions
     float oc_hi[3], oc_lo[3];  // the centre as an exact FP32 pair
     float q, inv_q;    // grid of the hi parts (a power of two)
@@ -111,9 +118,15 @@ __device__ __forceinline__ float unfix16(uint32_t u16, float s) {
     return fmaf(__int_as_float(0x4B000000u | u16), s, -8421376.f * s);
 }
 
-// Scale of the radius residual: ulp(R) / 2^15 for a normal R > 2^-87.
+// 12-bit field u (offset 2^11) scaled by s (a power of two), exactly (as
+// unfix16: (2^23 + u) s - (2^23 + 2^11) s).
+__device__ __forceinline__ float unfix12(uint32_t u12, float s) {
+    return fmaf(__int_as_float(0x4B000000u | u12), s, -8390656.f * s);
+}
+
+// Scale of the radius residual: ulp(R) / 2^11 for a normal R > 2^-91.
 __device__ __forceinline__ float rlo_scale(float R) {
-    return __int_as_float((int)(__float_as_uint(R) & 0x7F800000u) - ((23 + 15) << 23));
+    return __int_as_float((int)(__float_as_uint(R) & 0x7F800000u) - ((23 + 11) << 23));
 }
 
 // Position residuals and radius residual of a record: {x_lo, y_lo, z_lo, R_lo}
@@ -121,7 +134,22 @@ __device__ __forceinline__ float rlo_scale(float R) {
 __device__ __forceinline__ float4 record_lo(const float4 p, const float4 c, float qs) {
     const uint32_t wxy = __float_as_uint(c.z), wzr = __float_as_uint(c.w);
     return make_float4(unfix16(wxy & 0xFFFFu, qs), unfix16(wxy >> 16, qs), unfix16(wzr & 0xFFFFu, qs),
-                       unfix16(wzr >> 16, rlo_scale(p.w)));
+                       unfix12((wzr >> 16) & 0xFFFu, rlo_scale(p.w)));
+}
+
+// Cell type carried in a record's second half (0..15).
+__device__ __forceinline__ uint32_t record_type(const float4 c) { return __float_as_uint(c.w) >> 28; }
+
+// Upper 16 bits of lo_zr for a radius R (FP64) and a type: the residual
+// R - (float)R in units of ulp(R) / 2^11, offset 2^11, and the type above it.
+__host__ __device__ inline uint32_t radius_type_bits(double R, float Rf, uint32_t type) {
+    int e2 = 0;
+    frexpf(Rf, &e2);  // Rf = f 2^e2, f in [0.5, 1): ulp(Rf) = 2^(e2 - 24)
+    const double units = (R - (double)Rf) / ldexp(1.0, e2 - 24);
+    double t = units * 2048.0;
+    t = t < -2048.0 ? -2048.0 : (t > 2047.0 ? 2047.0 : t);
+    const long long L = llround(t);
+    return ((uint32_t)(L + 2048) | (type << 12)) << 16;
 }
 
 // Error-free sum: s + e == a + b exactly (Knuth).
@@ -164,6 +192,12 @@ struct StepArgs {
     float A2m1_f;          // A^2 - 1 (rounded once)
     double A_d, dt_d;
     int integrate;         // 1: AB2 update; 0: velocities only (positions kept)
+    // velocity variants (off: ntypes 0, walls 0)
+    int ntypes;            // > 0: per-type adhesion affinity, tables of 16 x 16 entries
+    const float* aff_f;    // affinity a[t_i][t_j] at 16 t_i + t_j (FP32 modes)
+    const double* aff_d;   // the same in FP64 (FP64 mode)
+    int walls;             // enabled faces: bit f for -x, +x, -y, +y, -z, +z
+    double c_wall;         // wall coefficient (um/min)
     float* vout_f;         // velocities-only output, B order (mixed modes)
     double* vout_d;        // velocities-only output, B order (FP64 mode)
     uint32_t* err;
@@ -218,11 +252,13 @@ cudaError_t launch_remove_in_place(const StepArgs& a, const uint8_t* alive, cons
 cudaError_t launch_compact_params(const StepArgs& a, const uint8_t* alive, const uint32_t* newid, double* io,
                                   cudaStream_t s);
 // New cell k of m goes to slot and caller index dst[k] of st: FP64
-// parameters (into R64, ccr64, cca64, caller order), force record, position
+// parameters (into R64, ccr64, cca64, caller order), force record (with its
+// type types[k], or 0 if types is null), position
 // (rounded as by mech_write_positions) and zero previous velocity, from io
 // (positions at [0, 3m), R, ccr, cca at [3m, 4m), [4m, 5m), [5m, 6m)).
 cudaError_t launch_append_state(const StepArgs& a, const StateBuf& st, const double* io, const uint32_t* dst,
-                                uint32_t m, double* R64, double* ccr64, double* cca64, cudaStream_t s);
+                                const uint32_t* types, uint32_t m, double* R64, double* ccr64, double* cca64,
+                                cudaStream_t s);
 // Batches: order-preserving removal from a.A into a.B (dst: exclusive prefix
 // of the keep flags over the state order), every replicate staying one range.
 cudaError_t launch_compact_state(const StepArgs& a, const uint8_t* alive, const uint32_t* dst, const uint32_t* newid,
@@ -345,6 +381,45 @@ __device__ __forceinline__ void warp_add(uint32_t* count, uint32_t key, bool val
     uint32_t k = valid ? key : 0xFFFFFFFFu;
     uint32_t grp = __match_any_sync(0xFFFFFFFFu, k);
     if (valid && lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(&count[key], (uint32_t)__popc(grp));
+}
+
+// Affinity factor of a pair of types (1 when the affinity is off).
+__device__ __forceinline__ float affinity_f(const StepArgs& a, uint32_t ti, uint32_t tj) {
+    return a.ntypes > 0 ? __ldg(&a.aff_f[ti * kMaxTypes + tj]) : 1.0f;
+}
+
+// Domain-wall terms of one cell (velocity variant), added to acc in face
+// order -x, +x, -y, +y, -z, +z, in FP64 with the definition's operations:
+// d_w = inward distance of the centre x from the face; if d_w < R,
+// t = 1 - d_w / R (t = 1 for d_w <= 0) and acc += c_w t^2 along the inward
+// normal.
+__device__ __forceinline__ void wall_terms(const StepArgs& a, const GridDev& g, const double x[3], double R,
+                                           double acc[3]) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        if (!(a.walls & (1 << f))) continue;
+        const int axis = f >> 1;
+        const bool high = (f & 1) != 0;
+        const double dw = high ? __dsub_rn(g.whi[axis], x[axis]) : __dsub_rn(x[axis], g.lo[axis]);
+        if (!(dw < R)) continue;
+        const double t = dw > 0.0 ? __dsub_rn(1.0, __ddiv_rn(dw, R)) : 1.0;
+        const double push = __dmul_rn(a.c_wall, __dmul_rn(t, t));
+        acc[axis] = high ? __dsub_rn(acc[axis], push) : __dadd_rn(acc[axis], push);
+    }
+}
+
+// Whether an FP32 position may lie within R + 1 um of an enabled face (a
+// conservative test: the FP32 rounding of a coordinate is far below 1 um).
+__device__ __forceinline__ bool near_wall(const StepArgs& a, const GridDev& g, const float xf[3], float R) {
+    bool near = false;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        if (!(a.walls & (1 << f))) continue;
+        const int axis = f >> 1;
+        const float dw = (f & 1) ? g.whi_f[axis] - xf[axis] : xf[axis] - g.lo_f[axis];
+        near = near || dw < R + 1.0f;
+    }
+    return near;
 }
 
 }  // namespace mk

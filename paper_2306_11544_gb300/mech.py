@@ -44,7 +44,7 @@ MODES = {"fp64": MECH_FP64, "mixed": MECH_MIXED_FP64POS, "fp64pos": MECH_MIXED_F
 EXPORTS = [
     "mech_last_error", "mech_version", "mech_create", "mech_create_batch", "mech_set_params",
     "mech_set_domain", "mech_set_precision", "mech_set_internal_voxel", "mech_set_launch",
-    "mech_set_tiling", "mech_set_dense_kernel", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
+    "mech_set_tiling", "mech_set_dense_kernel", "mech_set_affinity", "mech_set_walls", "mech_set_stream", "mech_set_graph", "mech_step", "mech_compute_velocities", "mech_set_profiling",
     "mech_read_profile", "mech_sync",
     "mech_read_positions", "mech_read_velocities", "mech_write_positions", "mech_read_state",
     "mech_load_state", "mech_remove_cells", "mech_add_cells", "mech_add_cells_batch", "mech_debug_bins",
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
             "mech_set_launch": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_set_tiling": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
             "mech_set_dense_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
+            "mech_set_affinity": ([_P, ctypes.c_int32, _P], ctypes.c_int),
+            "mech_set_walls": ([_P, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
             "mech_set_stream": ([_P, _P], ctypes.c_int),
             "mech_set_graph": ([_P, ctypes.c_int32], ctypes.c_int),
             "mech_step": ([_P, ctypes.c_int64], ctypes.c_int),
@@ -259,6 +261,22 @@ def mech_set_tiling(h, tile=(4, 4, 4), dense_min=12):
 def mech_set_dense_kernel(h, kernel):
     k = DENSE_KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     _check(load_library().mech_set_dense_kernel(h, k), "mech_set_dense_kernel")
+
+
+def mech_set_affinity(h, aff):
+    """aff: an ntypes x ntypes symmetric matrix, or None to switch the affinity off."""
+    if aff is None:
+        _check(load_library().mech_set_affinity(h, 0, None), "mech_set_affinity")
+        return
+    a = np.ascontiguousarray(aff, dtype=np.float64)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("affinity must be a square matrix")
+    _check(load_library().mech_set_affinity(h, int(a.shape[0]), a.ctypes.data_as(ctypes.c_void_p)),
+           "mech_set_affinity")
+
+
+def mech_set_walls(h, face_mask, c_wall):
+    _check(load_library().mech_set_walls(h, int(face_mask), float(c_wall)), "mech_set_walls")
 
 
 def mech_set_stream(h, stream):
@@ -450,6 +468,12 @@ class Mech:
 
     def set_dense_kernel(self, kernel):
         mech_set_dense_kernel(self.h, kernel)
+
+    def set_affinity(self, aff):
+        mech_set_affinity(self.h, aff)
+
+    def set_walls(self, face_mask, c_wall):
+        mech_set_walls(self.h, face_mask, c_wall)
 
     def set_stream(self, stream):
         mech_set_stream(self.h, stream)

@@ -65,6 +65,14 @@ def test_host_validation_needs_no_gpu(lib):
     assert lib.mech_create_batch(ctypes.byref(h), 2, p(counts), p(xyz), p(R), p(c), p(c), None) == mech.MECH_E_ARG
     assert lib.mech_create_batch(ctypes.byref(h), 0, p(counts), p(xyz), p(R), p(c), p(c), None) == mech.MECH_E_ARG
     assert b"replicate" in lib.mech_last_error() or b"n_rep" in lib.mech_last_error()
+    # cell types travel in 4 bits of the force record: outside [0, 16) is refused
+    for bad in ([0, 16], [-1, 2]):
+        t = np.array(bad, dtype=np.int32)
+        assert lib.mech_create(ctypes.byref(h), 2, p(xyz), p(R), p(c), p(c), p(t)) == mech.MECH_E_ARG
+        assert b"types" in lib.mech_last_error()
+    # variant setters refuse a null handle
+    assert lib.mech_set_affinity(None, 1, p(np.ones(1))) == mech.MECH_E_ARG
+    assert lib.mech_set_walls(None, 1, 1.0) == mech.MECH_E_ARG
 
 
 def test_binding_raises_without_library(tmp_path):
