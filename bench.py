@@ -111,32 +111,14 @@ def reduce_max(x: float, pg, device) -> float:
     return float(t.item())
 
 
-def shard_replicates(counts, world: int):
-    """Replicates of an ensemble split over `world` ranks with no exchange
-    between them: largest first, each to the rank with the fewest cells so far
-    (ties to the lower rank).  Returns each rank's replicate indices in
-    ascending order."""
-    if world > len(counts):
-        raise ValueError(f"{world} ranks for {len(counts)} replicates")
-    load = [0] * world
-    out = [[] for _ in range(world)]
-    for r in sorted(range(len(counts)), key=lambda i: (-int(counts[i]), i)):
-        k = min(range(world), key=lambda w: (load[w], w))
-        out[k].append(r)
-        load[k] += int(counts[r])
-    return [sorted(x) for x in out]
-
-
 def job_throughput(cells_per_rank: int, world: int, steps: int, seconds: float) -> float:
     """Whole-job cell-steps/s: every rank advances its own replica by `steps`."""
     return cells_per_rank * world * steps / seconds
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2306_11544_gb300 import shard
+    return shard.dist_env()
 
 
 def hbm_peak():
@@ -626,11 +608,12 @@ def main():
     if batched and ws > 1:
         # the ensemble's replicates are split over the ranks (strong scaling):
         # each rank steps its own batch, with no data-path exchange
-        parts = shard_replicates([p.n for p in wl.reps], ws)
+        from paper_2306_11544_gb300 import shard
+        parts = shard.shard_replicates([p.n for p in wl.reps], ws)
         total_cells = wl.n_total
         sharding = {"replicates_per_rank": [len(x) for x in parts],
                     "cells_per_rank": [int(sum(wl.reps[i].n for i in x)) for x in parts]}
-        wl = synth.Ensemble(wl.name, [wl.reps[i] for i in parts[rank]], wl.steps, dict(wl.meta))
+        wl, _ = shard.local_ensemble(wl, rank, ws)
     if not batched:
         m = mech.Mech.from_population(wl, mode=args.mode)
         n = wl.n

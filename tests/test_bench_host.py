@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import bench
-from paper_2306_11544_gb300 import synth
+from paper_2306_11544_gb300 import shard, synth
 
 
 def replay(pop, events):
@@ -44,12 +44,12 @@ def test_turnover_events_keep_the_count_and_follow_survivors():
 def test_replicate_sharding_covers_every_replicate_once_and_balances():
     counts = [p.n for p in synth.ensemble_256(seed=0, scale=0.01).reps]
     for world in (1, 2, 3, 8):
-        parts = bench.shard_replicates(counts, world)
+        parts = shard.shard_replicates(counts, world)
         flat = sorted(i for x in parts for i in x)
         assert flat == list(range(len(counts)))  # each replicate on exactly one rank
         loads = [sum(counts[i] for i in x) for x in parts]
         # greedy largest-first: no rank exceeds the mean by more than the largest replicate
         assert max(loads) - sum(counts) / world <= max(counts)
-        assert bench.shard_replicates(counts, world) == parts  # deterministic
+        assert shard.shard_replicates(counts, world) == parts  # deterministic
     with pytest.raises(ValueError):
-        bench.shard_replicates([5, 6], 3)
+        shard.shard_replicates([5, 6], 3)
