@@ -11,9 +11,16 @@ memory roofline the project is measured against.  Prints one JSON line.
 One step = one pass of the whole hot path (bin, force, AB2) over all cells.
 `value` is device-timed (CUDA events on the library's stream, state resident
 in HBM); `e2e` goes through the C ABI with the positions copied in from pinned
-host memory and read back every step.  Under torchrun every rank advances its
-own copy of the workload on its own GPU (independent replicas; the method
-needs no exchange between GPUs), and rank 0 reports the aggregate.
+host memory and read back every step.  `roofline` is the force phase against
+the measured HBM copy bandwidth with the fixed byte model (84 B/cell),
+`step_roofline` the whole step (228 B/cell + 20 B/voxel).  On one GPU the
+line also carries `second_arm` (the same workload in the other FP32 position
+mode: FP64 positions next to compensated FP32 ones) and `batched_vs_plain`
+(the 256-replicate ensemble advanced by one batched handle against the plain
+handles looped over the replicates, with and without a CUDA graph per
+handle).  Under torchrun every rank advances its own copy of the workload on
+its own GPU (independent replicas; the method needs no exchange between
+GPUs), and rank 0 reports the aggregate.
 """
 from __future__ import annotations
 
@@ -36,21 +43,6 @@ METRIC = "mechanics cell-steps/s (bin+force+AB2), batched vs plain, at <=1e-3 um
 UNIT = "cell-steps/s"
 # Algorithmic bytes (compulsory HBM traffic) of the fixed byte model.
 FORCE_BYTES_PER_CELL = 84      # read x 24 + params 12 + v_prev 12, write x 24 + v 12
-# Algorithmic FP32 operations of the force phase, by the method's definition:
-# every cell tests the cells of the 27 voxels around its voxel on the
-# workload's mechanics grid (8 operations: 3 differences, 3 multiply-adds, a
-# compare), each interacting ordered pair adds 30 (square root, reciprocals,
-# the two squared terms, scaling and accumulation), and the AB2 update of a
-# cell 15 (5 per component).  The internal grid the step uses is finer, so the
-# step performs fewer tests than the method's count; the count is the
-# method's, measured on the workload's grid after the timed region.
-OPS_PER_CANDIDATE = 8
-OPS_PER_ORDERED_PAIR = 30
-OPS_PER_CELL_AB2 = 15
-# FP32 peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 ops
-# (fused multiply-add) x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
 STEP_BYTES_PER_CELL = 228      # key+hist 28, scatter 116, force+AB2 84
 STEP_BYTES_PER_VOXEL = 20      # histogram zero/atomics 12, scan 8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -91,6 +83,11 @@ def parse():
                         "configs 1, 2, 3 and 5; prints one JSON line")
     p.add_argument("--plain-loop", action="store_true",
                    help="ensembles: also time the plain single-population path looped over replicates")
+    p.add_argument("--no-ensemble", action="store_true",
+                   help="single populations: skip the batched-vs-plain comparison on the 256-replicate ensemble")
+    p.add_argument("--ensemble-scale", type=float, default=1.0)
+    p.add_argument("--no-arm", action="store_true",
+                   help="single populations: skip the second precision arm (FP64 positions next to Kahan)")
     p.add_argument("--turnover", type=float, default=0.0,
                    help="single populations: also time a loop in which this fraction of the cells dies every "
                         "--turnover-every steps and as many daughters are added next to random survivors")
@@ -493,35 +490,113 @@ def time_turnover(m, pop, args, stream, torch, ms_per_step_plain):
                     "page-locked host arrays)"}
 
 
-def time_plain_loop(ens, args, stream, torch):
+def time_plain_loop(ens, args, stream, torch, steps=None, warmup=None, graph=0):
     """The plain single-population API looped over the replicates: one handle
-    per replicate, each advanced `steps` steps on the same stream."""
+    per replicate, each advanced `steps` steps on the same stream, first with
+    direct launches, then (graph > 0) with each handle replaying its own CUDA
+    graph of `graph` steps.  Returns {"ungraphed": ..., "graphed": ...}."""
     from paper_2306_11544_gb300 import mech
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    mode = getattr(args, "ens_mode", args.mode)
     hs = []
     for p in ens.reps:
-        h = mech.Mech.from_population(p, mode=args.mode)
+        h = mech.Mech.from_population(p, mode=mode)
         if args.voxel not in ("user", "0"):
-            h.set_internal_voxel(getattr(args, "voxel_value", p.h))
+            h.set_internal_voxel(2.0 * p.A * float(p.R.max()) * (1.0 + 1e-5) if args.voxel == "min"
+                                 else float(args.voxel))
         tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
         h.set_tiling(tile, args.dense_min)
+        h.set_dense_kernel(args.dense_kernel)
         h.set_stream(stream)
         hs.append(h)
+    n = sum(p.n for p in ens.reps)
+    out = {}
+    for kind, g in (("ungraphed", 0), ("graphed", graph)):
+        if kind == "graphed" and not graph:
+            continue
+        for h in hs:
+            h.set_graph(g)
+            h.step(max(warmup, 2 * g if g else warmup))  # also captures the graphs
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for h in hs:
+            h.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = sum(h.info()["launches_per_step"] for h in hs)
+        out[kind] = {"value": n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "handles": len(hs),
+                     "launches_per_step": launches, "graph_steps": g}
     for h in hs:
-        h.step(args.warmup)
+        h.close()
+    return out
+
+
+def ensemble_comparison(args, stream, torch):
+    """Batched versus plain on the 256-replicate ensemble (N_r log-uniform in
+    [1e3, 2e5], FP32 force / FP64 position): the batched handle replays one
+    graph holding all replicates; the plain arm loops the single-population
+    handles, with and without a graph per handle.  Both give the same
+    positions bit for bit (tests/test_gpu_parity.py), so the comparison is at
+    equal error."""
+    from paper_2306_11544_gb300 import mech, synth
+    ens = synth.ensemble_256(seed=0, scale=args.ensemble_scale)
+    steps = max(10, args.steps)
+    graph = 10 if steps % 10 == 0 else 2
+    m = mech.Mech.from_ensemble(ens, mode="mixed")
+    if args.voxel not in ("user", "0"):
+        m.set_internal_voxel(2.0 * ens.reps[0].A * max(float(p.R.max()) for p in ens.reps) * (1.0 + 1e-5))
+    tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
+    m.set_tiling(tile, args.dense_min)
+    m.set_dense_kernel(args.dense_kernel)
+    m.set_stream(stream)
+    m.set_graph(graph)
+    m.step(max(args.warmup, 2 * graph))
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for h in hs:
-        h.step(args.steps)
+    m.step(steps)
     ev1.record(stream)
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    n = sum(p.n for p in ens.reps)
-    launches = sum(h.info()["launches_per_step"] for h in hs)
-    for h in hs:
-        h.close()
-    return {"value": n * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "handles": len(hs), "launches_per_step": launches}
+    info = m.info()
+    m.close()
+    n = ens.n_total
+    batched = {"value": n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "graph_steps": graph,
+               "launches_per_step": info["launches_per_step"]}
+    args.ens_mode = "mixed"
+    plain = time_plain_loop(ens, args, stream, torch, steps=steps, warmup=args.warmup, graph=graph)
+    return {"workload": "ensemble_256", "replicates": len(ens.reps), "cells": n, "mode": "mixed", "steps": steps,
+            "scale": args.ensemble_scale, "batched": batched, "plain_graphed": plain["graphed"],
+            "plain_ungraphed": plain["ungraphed"],
+            "batched_over_plain_graphed": batched["value"] / plain["graphed"]["value"],
+            "batched_over_plain_ungraphed": batched["value"] / plain["ungraphed"]["value"]}
+
+
+def time_arm(wl, args, stream, torch, mode):
+    """Device time of the single-population step in another precision mode,
+    same launch configuration (the second arm of the 20M-cell configuration)."""
+    from paper_2306_11544_gb300 import mech
+    m = mech.Mech.from_population(wl, mode=mode)
+    if args.voxel not in ("user", "0"):
+        m.set_internal_voxel(args.voxel_value)
+    tile = tuple(int(x) for x in args.tile.split(",")) if args.tile != "0" else None
+    m.set_tiling(tile, args.dense_min)
+    m.set_dense_kernel(args.dense_kernel)
+    m.set_stream(stream)
+    m.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    m.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    m.close()
+    return {"mode": mode, "dtype": DTYPES[mode], "value": wl.n * args.steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.steps}
 
 
 def precision_study(args):
@@ -687,8 +762,9 @@ def main():
 
     plain = None
     if batched and args.plain_loop:
-        plain = time_plain_loop(wl, args, stream, torch)
-        plain["batched_over_plain"] = n * args.steps / (t_max * 1e-3) / plain["value"]  # this rank's replicates
+        plain = time_plain_loop(wl, args, stream, torch, graph=args.graph)
+        for kind in list(plain):
+            plain[kind]["batched_over_plain"] = n * args.steps / (t_max * 1e-3) / plain[kind]["value"]
 
     # end to end through the C ABI: pinned host positions in, step, positions out
     e2e = None
@@ -728,6 +804,14 @@ def main():
             m.set_internal_voxel(args.voxel_value)  # the step's own grid again
         turnover = time_turnover(m, wl, args, stream, torch, t_max / args.steps)
     m.close()
+    # the configuration's second precision arm and the batched-vs-plain
+    # ensemble comparison (one GPU runs: extra lines of the same job)
+    arm = None
+    if not batched and ws == 1 and not args.no_arm and args.mode in ("kahan", "mixed"):
+        arm = time_arm(wl, args, stream, torch, "mixed" if args.mode == "kahan" else "kahan")
+    ens_cmp = None
+    if not batched and ws == 1 and not args.no_ensemble:
+        ens_cmp = ensemble_comparison(args, stream, torch)
 
     if rank != 0:
         if pg:
@@ -737,35 +821,26 @@ def main():
     peak, peak_kind = hbm_peak()
     roof = None
     if profile and psteps:
-        # the force phase (velocity + AB2 kernels) dominates the step; its
-        # bound is instruction issue, so the roofline is the FP32 one, with the
-        # method's operation count from the neighbour statistics of the run
+        # the force phase (velocity + AB2 kernels) is the dominant part of the
+        # step; its algorithmic bytes are the fixed model's 84 B/cell
         t_force = (phases["classify"] + phases["tiles"] + phases["cells"]) / psteps * 1e-3
         cand, cand_done, pairs = stats
-        ops = OPS_PER_CANDIDATE * cand + OPS_PER_ORDERED_PAIR * 2 * pairs + OPS_PER_CELL_AB2 * n
-        ach = ops / t_force / 1e12
         tr = force_traffic()
         kern = ("k_force_fp64" if args.mode == "fp64"
                 else "force phase: k_tile_classify + k_force_tile + k_sparse_list + k_force_cells")
         bytes_alg = FORCE_BYTES_PER_CELL * n
-        alu_peak, alu_kind = ((FP64_PEAK_TFLOPS, "nominal FP64 rate of the part") if args.mode == "fp64" else
-                              (FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"))
-        roof = {"bound": "alu", "kernel": kern,
-                "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                "peak_kind": alu_kind,
-                "ops_per_launch": ops,
-                "ops_model": f"{OPS_PER_CANDIDATE}/neighbour test x {cand} (27 voxels of the workload's grid) + "
-                             f"{OPS_PER_ORDERED_PAIR}/ordered pair x {2 * pairs} + {OPS_PER_CELL_AB2}/cell AB2 x {n}",
-                "neighbour_tests_method": cand, "neighbour_tests_performed": cand_done,
-                "interacting_pairs": pairs,
+        roof = {"bound": "hbm", "kernel": kern,
+                "achieved": bytes_alg / t_force / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": bytes_alg / t_force / 1e9 / peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_launch": bytes_alg,
+                "bytes_model": f"{FORCE_BYTES_PER_CELL} B/cell (x 24, params 12, v_prev 12 in; x 24, v 12 out) x {n} cells",
                 "launch_ms": 1e3 * t_force,
                 "traffic": None if tr is None else tr.get("dram_bytes_per_cell", 0) * n,
                 "traffic_source": None if tr is None else tr.get("source"),
-                "hbm_view": {"bytes_per_launch": bytes_alg,
-                             "bytes_model": f"{FORCE_BYTES_PER_CELL} B/cell (x, params, v_prev in; x, v out)",
-                             "achieved": bytes_alg / t_force / 1e9, "peak": peak, "unit": "GB/s",
-                             "frac": bytes_alg / t_force / 1e9 / peak,
-                             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}}
+                "work": {"neighbour_tests_performed": cand_done, "neighbour_tests_on_workload_grid": cand,
+                         "interacting_pairs": pairs},
+                "note": "not bound by HBM: instruction issue (ncu: profiles/force_tile_clustered_20m_x0.25.md)"}
     # algorithmic model on the workload's own voxel grid (the internal grid the
     # autotuner may pick is a performance choice, not work of the problem)
     reps = [wl] if not batched else wl.reps
@@ -788,6 +863,10 @@ def main():
         "e2e": e2e,
         "gpu_launches": info["launches_per_step"] * args.steps,
     }
+    if arm is not None:
+        line["second_arm"] = arm
+    if ens_cmp is not None:
+        line["batched_vs_plain"] = ens_cmp
     if turnover is not None:
         line["turnover"] = turnover
     if sharding is not None:
@@ -799,7 +878,7 @@ def main():
             line["plain_looped"] = plain
     if tuned is not None:
         line["autotune"] = {"best": tuned["best"], "trials": [
-            {k: t[k] for k in ("voxel", "tile", "dense_min", "block", "ms_per_step")} for t in tuned["trials"]]}
+            {k: t[k] for k in (*autotune.KEYS, "ms_per_step")} for t in tuned["trials"]]}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -336,8 +336,20 @@ MECH_API int mech_pair_stats(mech_t* h, int64_t* candidates, int64_t* pairs);
  * library's device data, held by every GPU that loads the library until the
  * process exits; the call itself allocates and frees nothing.  The first call
  * on each device looks up the device address of that array
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Asynchronous: the outputs are ready when the
+ * (cudaGetSymbolAddress) with the device current; under lazy module loading
+ * (the CUDA default) that first use is also when the driver loads the
+ * library's device code and this array, which takes device memory.  So make
+ * the first call on each device early -- a call with n = 0 (xyz, key and
+ * order may then be NULL; start gets V + 1 zeros) does the set-up and nothing
+ * else of note -- before the caller's allocator reserves the device's memory
+ * and before any stream capture.
+ * Cost: the cells of a voxel are put in input order by ranking each one
+ * against the others of its voxel, so a voxel holding k cells costs k
+ * comparisons per cell; the lanes of a warp read the same entries together,
+ * so the whole call takes about sum over voxels of k^2 / 8 warp instructions
+ * on top of linear work: at tissue densities (under ~10 cells per voxel)
+ * linear, and at the limit of all 262,144 cells in one voxel about 8.6e9 warp
+ * instructions, tens of milliseconds.  Asynchronous: the outputs are ready when the
  * stream reaches this work.  Every call uses the same array and leaves its
  * contents behind, so calls whose work overlaps on the GPU (other streams,
  * other host threads) race and corrupt each other's results: serialise them.

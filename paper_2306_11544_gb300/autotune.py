@@ -1,5 +1,6 @@
-"""Autotuner for the mechanics step: internal voxel side, voxel-tile setting
-and thread-per-cell block size.
+"""Autotuner for the mechanics step: internal voxel side, voxel-tile setting,
+threads per voxel in dense tiles (one per target cell, or a warp of 32 per
+voxel) and thread-per-cell block size.
 
 For a handle (one population or a batch of replicates) it saves the exact
 state, times a few steps of each candidate setting with the library's own
@@ -18,7 +19,6 @@ from __future__ import annotations
 import json
 import math
 import os
-import subprocess
 import time
 
 import numpy as np
@@ -29,10 +29,11 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "mech_autotune.j
 
 
 def _gpu_name() -> str:
+    """Name and SM count of the current CUDA device (a runtime property query)."""
     try:
-        out = subprocess.run(["nvidia-smi", "--query-gpu=name", "--format=csv,noheader", "-i", "0"],
-                             capture_output=True, text=True, timeout=10)
-        return out.stdout.strip() or "unknown"
+        import torch
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{p.name}/{p.multi_processor_count}sm"
     except Exception:
         return "unknown"
 
@@ -46,22 +47,33 @@ def workload_key(n_cells: int, cells_per_um3: float, mode: int) -> str:
 def candidates(min_voxel: float, user_voxel: float):
     """Settings tried: voxel sides from the smallest valid one up to the user's,
     three tile shapes (two density thresholds for two of them) and no tiles,
-    two block sizes."""
+    the two dense-tile kernels (threads per voxel: one per target cell with
+    the halo in shared memory, or 32) for the common tile settings, two block
+    sizes."""
     up = lambda v: math.ceil(v * 1e4) / 1e4  # round up: never below the smallest valid side
     sides = sorted({up(min_voxel * f) for f in (1.0, 1.04, 1.1)} | {up(user_voxel)})
     sides = [s for s in sides if s <= max(up(user_voxel), up(min_voxel))]
     out = []
     for h in sides:
-        for tile, dmin in (((4, 4, 4), 12), ((4, 4, 4), 24), ((8, 4, 4), 16), ((4, 4, 8), 16), ((4, 4, 8), 48),
-                           (None, 0)):
-            for block in (128, 256):
-                out.append({"voxel": h, "tile": tile, "dense_min": dmin, "block": block})
+        for tile, dmin, kernels in (((4, 4, 4), 12, ("block_per_tile", "warp_per_voxel")),
+                                    ((4, 4, 4), 24, ("block_per_tile",)),
+                                    ((8, 4, 4), 16, ("block_per_tile", "warp_per_voxel")),
+                                    ((4, 4, 8), 16, ("block_per_tile",)), ((4, 4, 8), 48, ("block_per_tile",)),
+                                    (None, 0, ("block_per_tile",))):
+            for kernel in kernels:
+                for block in (128, 256):
+                    out.append({"voxel": h, "tile": tile, "dense_min": dmin, "dense_kernel": kernel,
+                                "block": block})
     return out
+
+
+KEYS = ("voxel", "tile", "dense_min", "dense_kernel", "block")
 
 
 def apply(m: "mech.Mech", cfg: dict) -> None:
     m.set_internal_voxel(cfg["voxel"])
     m.set_tiling(cfg["tile"], cfg["dense_min"] or 32)
+    m.set_dense_kernel(cfg.get("dense_kernel", "block_per_tile"))
     m.set_launch(cfg["block"])
 
 
@@ -109,11 +121,11 @@ def autotune(m: "mech.Mech", min_voxel: float, user_voxel: float, steps: int = 8
                 print(f"autotune {cfg} -> {ms:.3f} ms/step")
     best_of = {}
     for t in trials:
-        k = json.dumps({c: t[c] for c in ("voxel", "tile", "dense_min", "block")}, sort_keys=True)
+        k = json.dumps({c: t[c] for c in KEYS}, sort_keys=True)
         if k not in best_of or t["ms_per_step"] < best_of[k]["ms_per_step"]:
             best_of[k] = t
     best = min(best_of.values(), key=lambda t: t["ms_per_step"])
-    best_cfg = {k: best[k] for k in ("voxel", "tile", "dense_min", "block")}
+    best_cfg = {k: best[k] for k in KEYS}
     apply(m, best_cfg)
     m.load_state(saved)
     if key is not None:

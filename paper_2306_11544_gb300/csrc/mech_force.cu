@@ -31,6 +31,7 @@
 // and records are used as staged, with no per-tile frame shift.  No FP64
 // arithmetic runs in any candidate loop (FP64 is ~1/62 of FP32 throughput on
 // this GPU).
+#include <algorithm>
 #include <atomic>
 
 #include "mech_internal.cuh"
@@ -1280,7 +1281,7 @@ int tile_kernel_grid(const StepArgs& a, int sms) {
 cudaError_t launch_tile_classify(const StepArgs& a, cudaStream_t s) {
     if (a.ntiles == 0) return cudaSuccess;
     int g = (int)((a.ntiles + 255u) / 256u);
-    if (g > 152 * 16) g = 152 * 16;
+    g = std::min(g, device_sms() * 16);
     k_tile_classify<<<g, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

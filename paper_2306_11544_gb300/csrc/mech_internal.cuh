@@ -224,6 +224,10 @@ struct StepArgs {
 // Host-armed fault injection (never set in normal runs).
 constexpr uint32_t kFaultTileWait = 1u;  // the tile kernel's TMA barrier expects 16 bytes too many
 
+// Streaming multiprocessors of the current device (queried once per device;
+// grid caps of the grid-stride kernels are multiples of it).
+int device_sms();
+
 // ---- launch wrappers (mech_bin.cu) ----
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
 cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);

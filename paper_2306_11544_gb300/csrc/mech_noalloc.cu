@@ -149,7 +149,8 @@ extern "C" int mech_bin_noalloc(int64_t n, const double* xyz, const double lo[3]
     uint32_t* slot = scratch + kNaSlot;
     uint32_t* tmp = scratch + kNaTmp;
     const uint32_t nn = (uint32_t)n;
-    const int grid = nn ? (int)std::min<uint32_t>((nn + 255) / 256, 152 * 8) : 1;
+    const uint32_t gcap = (uint32_t)device_sms() * 8u;
+    const int grid = nn ? (int)std::min<uint32_t>((nn + 255) / 256, gcap) : 1;
     cudaError_t e = launch_zero_u32(count, vpad, s);  // the histogram must start from zero on every call
     if (e == cudaSuccess && nn) {
         k_na_keys<<<grid, 256, 0, s>>>(nn, xyz, lo[0], lo[1], lo[2], 1.0 / voxel, dims[0], dims[1], dims[2], count,
@@ -167,7 +168,7 @@ extern "C" int mech_bin_noalloc(int64_t n, const double* xyz, const double lo[3]
     }
     if (e == cudaSuccess) {
         const uint32_t cnt = (uint32_t)V + 1;
-        k_na_copy<<<(int)std::min<uint32_t>((cnt + 255) / 256, 152 * 8), 256, 0, s>>>(cnt, sstart, start);
+        k_na_copy<<<(int)std::min<uint32_t>((cnt + 255) / 256, gcap), 256, 0, s>>>(cnt, sstart, start);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess)

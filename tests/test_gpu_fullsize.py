@@ -1,17 +1,22 @@
-"""Parity at the full sizes of the benchmark workloads.
+"""Parity at the full sizes of the benchmark workloads, against the CPU oracle.
 
-* 1M-cell spheroid (three cell types, lognormal radii): the FP64 mode's first
-  step is bit-identical to the oracle on every cell; over the workload's 1,000
-  steps the two mixed modes stay within 1e-3 um of the FP64 mode.  Because the
-  FP64 mode reproduces the oracle's every operation in order (checked here and
-  in test_gpu_parity.py), its trajectory is the oracle's trajectory; running
-  the oracle itself for 1e9 cell-steps would take many CPU minutes.
+* 1M-cell spheroid (three cell types, lognormal radii), the workload's 1,000
+  steps: the oracle's trajectory is computed on the host (about 150 s on 16
+  cores); the FP64 mode ends bit-identical to it and both FP32 modes within
+  1e-3 um of it.
 * 20M-cell clustered workload in the launch configuration bench.py times
-  (Kahan positions, smallest internal voxel, 4x4x4 tiles): velocities of
-  sampled cells (core, shell, core surface) against the oracle, computed cell
-  by cell, plus properties that hold at any size (finite state, zero net
-  velocity to rounding level).
+  (smallest internal voxel, 4x4x4 tiles): a 5-step prefix of its 200 steps
+  against the oracle run on the host (about a minute), both FP32 modes within
+  1e-3 um; velocities of sampled cells (core, shell, core surface) against
+  the oracle cell by cell; properties that hold at any size (finite state,
+  zero net velocity to rounding level); and the whole 200 steps against the
+  FP64 mode (whose every step is the oracle's, as the tests above show).
+* The long-horizon configuration (32 replicates, 10,000 steps): its smallest
+  replicate over all 10,000 steps in both FP32 modes against the oracle
+  (about 15 minutes of host time, so it runs only when MECH_LONG_PARITY=1).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -41,19 +46,56 @@ def test_spheroid_1m_fp64_first_step_bit_identical(spheroid_1m):
     assert np.array_equal(v, vref)
 
 
-def test_spheroid_1m_mixed_modes_over_1000_steps(spheroid_1m):
+def test_spheroid_1m_over_1000_steps_against_the_oracle(spheroid_1m):
     pop = spheroid_1m
     steps = pop.steps
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, steps)
     with H.make(pop, "fp64") as m:
         m.step(steps)
-        xr = m.positions()
+        x64 = m.positions()
+    assert np.array_equal(x64, xr), float(np.abs(x64 - xr).max())
     errs = {}
     for mode in ("mixed", "kahan"):
         with H.make(pop, mode) as m:
             m.step(steps)
             x = m.positions()
         errs[mode] = float(np.abs(x - xr).max())
-    print(f"spheroid_1m, {steps} steps, max |x - x_fp64| (um): {errs}")
+    print(f"spheroid_1m, {steps} steps, max |x - x_oracle| (um): {errs}")
+    for mode, e in errs.items():
+        assert e <= H.TOL_X_MIXED, (mode, e)
+
+
+def test_clustered_20m_prefix_against_the_oracle():
+    pop = synth.clustered_20m(seed=0)
+    steps = 5
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, steps)
+    errs = {}
+    for mode in ("mixed", "kahan"):
+        with H.make(pop, mode, voxel=hmin) as m:
+            m.set_tiling((4, 4, 4), 12)
+            m.step(steps)
+            errs[mode] = float(np.abs(m.positions() - xr).max())
+    print(f"clustered_20m, first {steps} steps, max |x - x_oracle| (um): {errs}")
+    for mode, e in errs.items():
+        assert e <= H.TOL_X_MIXED, (mode, e)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("MECH_LONG_PARITY") != "1", reason="about 15 min of host time; MECH_LONG_PARITY=1")
+def test_long_horizon_smallest_replicate_against_the_oracle():
+    ens = synth.ensemble_32_long(seed=0)
+    pop = min(ens.reps, key=lambda p: p.n)
+    steps = ens.steps
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop), pop.dt, steps)
+    hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
+    errs = {}
+    for mode in ("mixed", "kahan"):
+        with H.make(pop, mode, voxel=hmin) as m:
+            m.set_graph(100)
+            m.step(steps)
+            errs[mode] = float(np.abs(m.positions() - xr).max())
+    print(f"ensemble_32_long smallest replicate ({pop.n} cells), {steps} steps, max |x - x_oracle| (um): {errs}")
     for mode, e in errs.items():
         assert e <= H.TOL_X_MIXED, (mode, e)
 

@@ -396,8 +396,9 @@ def test_autotuner_restores_state_and_stays_correct():
     from paper_2306_11544_gb300 import autotune
     pop = synth.clustered_20m(seed=13, scale=0.002)
     hmin = 2 * pop.A * pop.R.max() * (1 + 1e-5)
-    cfgs = [{"voxel": hmin, "tile": (4, 4, 4), "dense_min": 16, "block": 128},
-            {"voxel": pop.h, "tile": None, "dense_min": 0, "block": 256}]
+    cfgs = [{"voxel": hmin, "tile": (4, 4, 4), "dense_min": 16, "dense_kernel": "block_per_tile", "block": 128},
+            {"voxel": hmin, "tile": (4, 4, 4), "dense_min": 16, "dense_kernel": "warp_per_voxel", "block": 128},
+            {"voxel": pop.h, "tile": None, "dense_min": 0, "dense_kernel": "block_per_tile", "block": 256}]
     with H.make(pop, "kahan") as m:
         m.step(2)
         before = m.read_state()
@@ -405,7 +406,7 @@ def test_autotuner_restores_state_and_stays_correct():
         after = m.read_state()
         for k in ("xyz", "vprev", "comp"):
             assert np.array_equal(before[k], after[k]), k
-        assert res["best"] in cfgs and len(res["trials"]) == 4
+        assert res["best"] in cfgs and len(res["trials"]) == 6
         assert m.info()["voxel"] == pytest.approx(res["best"]["voxel"])
         x = m.positions()
         m.step(1)
