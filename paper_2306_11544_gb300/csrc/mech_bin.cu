@@ -7,6 +7,9 @@
 // spatial neighbours are memory neighbours, and a voxel costs work only in
 // proportion to the cells it holds.  Order inside a voxel is ascending caller
 // index, which makes the permutation a function of the positions alone.
+#include <algorithm>
+#include <atomic>
+
 #include "mech_internal.cuh"
 
 namespace mk {
@@ -525,16 +528,27 @@ __global__ void k_load_vprev(const StepArgs a, const StateBuf st, const double* 
 int elementwise_grid(uint32_t n) {
     int g = (int)((n + 255u) / 256u);
     if (g < 1) g = 1;
-    if (g > 152 * 16) g = 152 * 16;
-    return g;
+    return std::min(g, device_sms() * 16);
 }
 
 }  // namespace
 
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];  // 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
     int g = (int)((count + 255) / 256);
-    if (g > 152 * 32) g = 152 * 32;
+    g = std::min(g, device_sms() * 32);
     k_zero_u32<<<g, 256, 0, s>>>(p, count);
     return cudaGetLastError();
 }
