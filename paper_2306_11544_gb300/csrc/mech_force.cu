@@ -33,6 +33,7 @@
 // this GPU).
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "mech_internal.cuh"
 
@@ -326,6 +327,7 @@ __device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, 
 // A cell alone in its voxel leaves that voxel out (it holds only the skipped
 // self pair), so an isolated cell walks no run at all.  Candidates are tested
 // on the hi parts; a pair that passes is evaluated from hi + lo.
+template <bool AFF>
 __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& g, const Cell3& c, uint32_t q,
                                               bool alone, const float4 pi, const float4 qi, Acc3& acc) {
     const float A = a.A_f;
@@ -371,8 +373,9 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
                 if (j != q && candidate_hit(hx, hy, hz, A, pj.w, cut_i)) {
                     const float4 qj = a.B.rec[2 * (size_t)j + 1];
                     const float4 lj = record_lo(pj, qj, g.qs);
+                    const float aij = AFF ? __ldg(&a.aff_f[record_type(qi) * kMaxTypes + record_type(qj)]) : 1.0f;
                     pair_term(hx, hy, hz, li.x - lj.x, li.y - lj.y, li.z - lj.z, pi.w, pj.w, li.w + lj.w, qi.x, qi.y,
-                              qj.x, qj.y, affinity_f(a, record_type(qi), record_type(qj)), A, a.A2m1_f, acc);
+                              qj.x, qj.y, aij, A, a.A2m1_f, acc);
                 }
             }
         }
@@ -384,7 +387,7 @@ __device__ __forceinline__ void velocity_walk(const StepArgs& a, const GridDev& 
 // all cells when tiles are off.  (Claiming 32 listed cells at a time from a
 // cursor instead of the static grid-stride assignment measured slower: the
 // claim's round trip lengthens every iteration of this latency-bound loop.)
-template <int MODE>
+template <int MODE, bool AFF>
 __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -411,11 +414,15 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
             const GridDev& g = a.grids[r];
             const Cell3 c = decode(key, g);
             Acc3 acc;
-            const float4 pq = a.B.rec[2 * (size_t)q], cq = a.B.rec[2 * (size_t)q + 1];
-            velocity_walk(a, g, c, q, alone, pq, cq, acc);
+            velocity_walk<AFF>(a, g, c, q, alone, a.B.rec[2 * (size_t)q], a.B.rec[2 * (size_t)q + 1], acc);
+            float Rf = 0.f, Rlo = 0.f;  // the radius, for the wall terms only
+            if (a.walls) {
+                const float4 pq = a.B.rec[2 * (size_t)q], cq = a.B.rec[2 * (size_t)q + 1];
+                Rf = pq.w;
+                Rlo = record_lo(pq, cq, g.qs).w;
+            }
             int nix, niy, niz;
-            nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), pq.w, record_lo(pq, cq, g.qs).w, nix,
-                                   niy, niz);
+            nkey = ab2_apply<MODE>(a, g, q, st, acc.vx(), acc.vy(), acc.vz(), Rf, Rlo, nix, niy, niz);
             ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
         }
         next_step_counts(a, q, nkey, ntile, valid);
@@ -1023,20 +1030,31 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                                     << k2;
                         }
                     }
-                    while (m[0] | m[1] | m[2]) {
-                        const int b = m[0] ? 0 : (m[1] ? 1 : 2);
-                        const uint32_t mb = b == 0 ? m[0] : (b == 1 ? m[1] : m[2]);
-                        const uint32_t k2 = (uint32_t)(__ffs(mb) - 1);
-                        const uint32_t rest = mb & (mb - 1u);
-                        if (b == 0) m[0] = rest; else if (b == 1) m[1] = rest; else m[2] = rest;
-                        const uint32_t jj = clist[cb + 32u * (uint32_t)b + k2];
-                        const float4 p2 = srec[2 * jj];
-                        const float4 q2 = srec[2 * jj + 1];
-                        const float4 l2 = record_lo(p2, q2, g.qs);
-                        pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y, li.z - l2.z, pi.w,
-                                  p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y,
-                                  affinity_f(a, record_type(qi), record_type(q2)), A, a.A2m1_f, acc);
-                    }
+                    // the hit loop, specialised on the affinity table (without
+                    // one, the factor is the literal 1 and costs nothing)
+                    auto hits = [&](auto with_affinity) {
+                        constexpr bool kAff = decltype(with_affinity)::value;
+                        while (m[0] | m[1] | m[2]) {
+                            const int b = m[0] ? 0 : (m[1] ? 1 : 2);
+                            const uint32_t mb = b == 0 ? m[0] : (b == 1 ? m[1] : m[2]);
+                            const uint32_t k2 = (uint32_t)(__ffs(mb) - 1);
+                            const uint32_t rest = mb & (mb - 1u);
+                            if (b == 0) m[0] = rest; else if (b == 1) m[1] = rest; else m[2] = rest;
+                            const uint32_t jj = clist[cb + 32u * (uint32_t)b + k2];
+                            const float4 p2 = srec[2 * jj];
+                            const float4 q2 = srec[2 * jj + 1];
+                            const float4 l2 = record_lo(p2, q2, g.qs);
+                            const float aij =
+                                kAff ? __ldg(&a.aff_f[record_type(qi) * kMaxTypes + record_type(q2)]) : 1.0f;
+                            pair_term(pi.x - p2.x, pi.y - p2.y, pi.z - p2.z, li.x - l2.x, li.y - l2.y,
+                                      li.z - l2.z, pi.w, p2.w, li.w + l2.w, qi.x, qi.y, q2.x, q2.y, aij, A,
+                                      a.A2m1_f, acc);
+                        }
+                    };
+                    if (a.ntypes > 0)
+                        hits(std::true_type{});
+                    else
+                        hits(std::false_type{});
                 }
                 int nix, niy, niz;
                 nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), pi.w, li.w, nix, niy, niz);
@@ -1262,9 +1280,9 @@ int force_max_blocks_per_sm(int mode, int block) {
     if (mode == kFP64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_fp64, block, 0);
     else if (mode == kMixedFP64Pos)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedFP64Pos>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedFP64Pos, false>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedKahan>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_cells<kMixedKahan, false>, block, 0);
     return nb > 0 ? nb : 1;
 }
 
@@ -1312,10 +1330,14 @@ cudaError_t launch_force_cells(const StepArgs& a, int grid, int block, cudaStrea
     if (a.n == 0) return cudaSuccess;
     if (a.mode == kFP64)
         k_force_fp64<<<grid, block, 0, s>>>(a);
+    else if (a.mode == kMixedFP64Pos && a.ntypes > 0)
+        k_force_cells<kMixedFP64Pos, true><<<grid, block, 0, s>>>(a);
     else if (a.mode == kMixedFP64Pos)
-        k_force_cells<kMixedFP64Pos><<<grid, block, 0, s>>>(a);
+        k_force_cells<kMixedFP64Pos, false><<<grid, block, 0, s>>>(a);
+    else if (a.ntypes > 0)
+        k_force_cells<kMixedKahan, true><<<grid, block, 0, s>>>(a);
     else
-        k_force_cells<kMixedKahan><<<grid, block, 0, s>>>(a);
+        k_force_cells<kMixedKahan, false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
