@@ -10,26 +10,42 @@
 //   shared equally: along a line of n voxels, with k = D dt / dx^2 and
 //   e = lambda dt / 3, the tridiagonal system has diagonal 1 + 2k + e inside,
 //   1 + k + e at the two faces (a mirrored neighbour: no flux), 1 + e for
-//   n = 1, and off-diagonals -k.  It is solved by the Thomas algorithm with
-//   coefficients shared by all lines of an axis, the pivots inverted once:
+//   n = 1, and off-diagonals -k.  It is solved by Gaussian elimination
+//   without pivoting (the Thomas algorithm), with coefficients shared by all
+//   lines of an axis and the pivots inverted once:
 //      m_0 = T_00;  m_i = T_ii + k c_{i-1} (i >= 1);  w_i = 1 / m_i;
 //      c_i = -k w_i
-//      forward  r_0 = old_0 w_0;  r_i = (old_i + k r_{i-1}) w_i
-//      backward r_i = r_i - c_i r_{i+1}   (i = n-2 .. 0)
 //   (no division inside the recurrences: an FP64 division costs about six
-//   FP64 additions on this GPU; the plain elimination divides by m_i, and the
-//   two arrangements agree to rounding), in FP64 with IEEE operations in this
-//   order (no contraction), so every value is reproducible run to run.  Gradients: central differences inside, one-sided
-//   at the faces, zero along an axis of one voxel; array [s][axis][v].
+//   FP64 additions on this GPU), in its two-ended form: the matrix reads the
+//   same from either end (T_ii = T_{n-1-i,n-1-i}), so eliminating upward from
+//   the last row produces the same pivots in mirror order, bit for bit.  With
+//   p = floor(n / 2):
+//      top    y_0 = old_0 w_0;  y_i = (old_i + k y_{i-1}) w_i        (i < p)
+//      bottom z_{n-1} = old_{n-1} w_0;
+//             z_i = (old_i + k z_{i+1}) w_{n-1-i}                  (i > p)
+//      meet   u_p = ((old_p + k y_{p-1}) + k z_{p+1}) / g,
+//             g = T_pp + k c_{p-1} + k c_{n-2-p}
+//             (a term is absent when its row is: p = 0, or p = n - 1)
+//      back   u_i = y_i - c_i u_{i+1} (i = p-1 .. 0);
+//             u_i = z_i - c_{n-1-i} u_{i-1} (i = p+1 .. n-1)
+//   The solution is that of the one-ended elimination up to rounding, and a
+//   line's dependent chain is n steps instead of 2 n: two threads share a
+//   line, one per end.  FP64 with IEEE operations in this order (no
+//   contraction), so every value is reproducible run to run.  Gradients:
+//   central differences inside, one-sided at the faces, zero along an axis of
+//   one voxel; array [s][axis][v].
 //
-// GB300 mapping: the work is a set of independent recurrences (one per grid
-// line), so every kernel runs one thread per line.  Lines along y and z are
-// strided in memory but their neighbours along x are adjacent, so a warp's 32
-// lines make coalesced accesses at every step of the recurrence.  Lines along
-// x are contiguous, so a warp first stages its 32 lines (one contiguous run of
-// memory) in shared memory with coalesced loads, solves there, and writes them
-// back.  A 75^3 field of a few substrates (3.4 MB each) stays in L2 between
-// the three solves.
+// GB300 mapping: the work is a set of independent recurrences (one per end
+// of a grid line), so every kernel runs two threads per line.  Lines along y
+// and z are strided in memory but their neighbours along x are adjacent: a
+// warp takes 16 adjacent lines, lanes 0-15 their top ends and lanes 16-31
+// their bottom ends, so every step of the recurrence is two coalesced
+// 128-byte accesses, and the two ends meet through one shuffle.  Lines along
+// x are contiguous, so a block of two warps first stages 32 lines (one
+// contiguous run of memory) in shared memory with coalesced loads; warp 0
+// solves their top ends and warp 1 their bottom ends there, and the block
+// writes them back.  A 75^3 field of a few substrates (3.4 MB each) stays in
+// L2 between the three solves.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,13 +65,24 @@
 
 namespace {
 
-constexpr int kLineTile = 32;   // x lines staged per warp
-constexpr int kMaxNxTile = 191;  // 32 lines of up to 191 doubles (+1 pad) fit in 48 KB of shared memory
+constexpr int kLineTile = 32;   // x lines staged per block (two warps: one per line end)
+constexpr int kMaxNxTile = 189;  // 32 lines of up to 189 doubles (odd stride) and the meeting values fit in 48 KB
+constexpr int kLinesPerWarp = 16;  // y/z and long x lines: 16 lines per warp, both ends
 
-// Thomas coefficients of one (substrate, axis) pair t = 3 s + axis.
+// Diagonal entry i of the tridiagonal matrix of a line of n voxels.
+__device__ __forceinline__ double diag_entry(int64_t i, int64_t n, double k, double e) {
+    if (n == 1) return __dadd_rn(1.0, e);
+    if (i == 0 || i == n - 1) return __dadd_rn(__dadd_rn(1.0, k), e);
+    return __dadd_rn(__dadd_rn(1.0, __dmul_rn(2.0, k)), e);
+}
+
+// Coefficients of one (substrate, axis) pair t = 3 s + axis: reciprocal
+// pivots w (in m) and c, nmax each; the reciprocal of the meeting row's pivot
+// g (in gi); and k per substrate.
 __device__ __forceinline__ void coeffs_one(int64_t t, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx,
                                            double dt, const double* __restrict__ D, const double* __restrict__ lam,
-                                           double* __restrict__ m, double* __restrict__ c, double* __restrict__ kk) {
+                                           double* __restrict__ m, double* __restrict__ c, double* __restrict__ gi,
+                                           double* __restrict__ kk) {
     const int64_t s = t / 3, a = t - 3 * s;
     const int64_t n = a == 0 ? nx : (a == 1 ? ny : nz);
     const double k = __ddiv_rn(__dmul_rn(D[s], dt), __dmul_rn(dx, dx));
@@ -64,101 +91,179 @@ __device__ __forceinline__ void coeffs_one(int64_t t, int64_t nx, int64_t ny, in
     double* mm = m + (size_t)t * nmax;
     double* cc = c + (size_t)t * nmax;
     for (int64_t i = 0; i < n; ++i) {
-        double diag;
-        if (n == 1) diag = __dadd_rn(1.0, e);
-        else if (i == 0 || i == n - 1) diag = __dadd_rn(__dadd_rn(1.0, k), e);
-        else diag = __dadd_rn(__dadd_rn(1.0, __dmul_rn(2.0, k)), e);
+        const double diag = diag_entry(i, n, k, e);
         const double piv = i == 0 ? diag : __dadd_rn(diag, __dmul_rn(k, cc[i - 1]));
         mm[i] = __ddiv_rn(1.0, piv);
         if (i < n - 1) cc[i] = __dmul_rn(-k, mm[i]);
     }
+    const int64_t p = n >> 1;
+    double g = diag_entry(p, n, k, e);
+    if (p >= 1) g = __dadd_rn(g, __dmul_rn(k, cc[p - 1]));
+    if (p <= n - 2) g = __dadd_rn(g, __dmul_rn(k, cc[n - 2 - p]));
+    gi[t] = __ddiv_rn(1.0, g);
 }
 
-// Thomas coefficients of every (substrate, axis): reciprocal pivots w (in m)
-// and c, nmax each; and k per substrate.  A grid-stride loop over the 3 S
+// Coefficients of every (substrate, axis): a grid-stride loop over the 3 S
 // (substrate, axis) pairs, one thread each.
 __global__ void k_diff_coeffs(int32_t S, int64_t nx, int64_t ny, int64_t nz, int64_t nmax, double dx, double dt,
                               const double* __restrict__ D, const double* __restrict__ lam, double* __restrict__ m,
-                              double* __restrict__ c, double* __restrict__ kk) {
+                              double* __restrict__ c, double* __restrict__ gi, double* __restrict__ kk) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * (int64_t)S;
          t += (int64_t)gridDim.x * blockDim.x)
-        coeffs_one(t, nx, ny, nz, nmax, dx, dt, D, lam, m, c, kk);
+        coeffs_one(t, nx, ny, nz, nmax, dx, dt, D, lam, m, c, gi, kk);
 }
 
-// One line of n values at p[0], p[stride], ... in place (any memory space);
-// w holds the reciprocal pivots.
-__device__ __forceinline__ void thomas(double* p, int64_t stride, int64_t n, double k, const double* __restrict__ w,
-                                       const double* __restrict__ c) {
-    double prev = __dmul_rn(p[0], w[0]);
-    p[0] = prev;
-    for (int64_t i = 1; i < n; ++i) {
-        prev = __dmul_rn(__dadd_rn(p[i * stride], __dmul_rn(k, prev)), w[i]);
-        p[i * stride] = prev;
+// One end of a line of n values (any memory space): the top end is rows
+// 0 .. p-1 from base = row 0 with step +stride, the bottom end rows
+// n-1 .. p+1 from base = row n-1 with step -stride; row j of an end (j-th
+// from its extremity) has pivot w_j and back coefficient c_j.
+struct LineEnd {
+    double* base;
+    int64_t step;
+    int64_t cnt;  // rows of this end: p (top) or n - 1 - p (bottom)
+};
+
+__device__ __forceinline__ LineEnd line_end(double* row0, int64_t stride, int64_t n, bool top) {
+    const int64_t p = n >> 1;
+    return top ? LineEnd{row0, stride, p} : LineEnd{row0 + (n - 1) * stride, -stride, n - 1 - p};
+}
+
+// Elimination toward the meeting row; returns the last value (0 without rows).
+__device__ __forceinline__ double end_eliminate(const LineEnd& L, double k, const double* __restrict__ w) {
+    double prev = 0.0;
+    for (int64_t j = 0; j < L.cnt; ++j) {
+        const double r = L.base[j * L.step];
+        prev = j == 0 ? __dmul_rn(r, w[0]) : __dmul_rn(__dadd_rn(r, __dmul_rn(k, prev)), w[j]);
+        L.base[j * L.step] = prev;
     }
-    double next = prev;
-    for (int64_t i = n - 2; i >= 0; --i) {
-        next = __dsub_rn(p[i * stride], __dmul_rn(c[i], next));
-        p[i * stride] = next;
+    return prev;
+}
+
+// Value of the meeting row from its right-hand side and the two ends' last values.
+__device__ __forceinline__ double meet(double rp, double k, double y, double z, double gi) {
+    return __dmul_rn(__dadd_rn(__dadd_rn(rp, __dmul_rn(k, y)), __dmul_rn(k, z)), gi);
+}
+
+// Back substitution from the meeting row out to the end's extremity.
+__device__ __forceinline__ void end_back(const LineEnd& L, const double* __restrict__ c, double up) {
+    double next = up;
+    for (int64_t j = L.cnt - 1; j >= 0; --j) {
+        next = __dsub_rn(L.base[j * L.step], __dmul_rn(c[j], next));
+        L.base[j * L.step] = next;
     }
 }
 
-// x lines: line L = (s nz + z) ny + y occupies rho[L nx, (L + 1) nx).  A warp
-// stages lines [L0, L0 + 32) (one contiguous run) in shared memory, each lane
-// solves one, and the warp writes them back.  The shared row stride is odd
-// (in doubles), so the 16 lanes of a half-warp hit 16 different banks.
-__global__ void __launch_bounds__(kLineTile) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
-                                                           int64_t ny, int64_t nz, int64_t nmax,
-                                                           const double* __restrict__ m, const double* __restrict__ c,
-                                                           const double* __restrict__ kk) {
+// x lines: line L = (s nz + z) ny + y occupies rho[L nx, (L + 1) nx).  A
+// block stages lines [L0, L0 + 32) (one contiguous run) in shared memory;
+// thread (line l = tid mod 32, end = tid / 32) solves one end of line l, the
+// ends meet through shared memory, and the block writes the lines back.  The
+// shared row stride is odd (in doubles), so the 16 lanes of a half-warp hit
+// 16 different banks.
+__global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
+                                                               int64_t ny, int64_t nz, int64_t nmax,
+                                                               const double* __restrict__ m,
+                                                               const double* __restrict__ c,
+                                                               const double* __restrict__ gi,
+                                                               const double* __restrict__ kk) {
     extern __shared__ double tile[];
+    __shared__ double s_last[2 * kLineTile];
     const int64_t stride = nx | 1;
-    const int lane = threadIdx.x;
+    const int l = threadIdx.x & (kLineTile - 1);
+    const bool top = threadIdx.x < kLineTile;
+    const int64_t p = nx >> 1;
     for (int64_t L0 = (int64_t)blockIdx.x * kLineTile; L0 < lines; L0 += (int64_t)gridDim.x * kLineTile) {
         const int64_t cnt = lines - L0 < kLineTile ? lines - L0 : kLineTile;
         const double* src = rho + L0 * nx;
-        for (int64_t w = lane; w < cnt * nx; w += kLineTile) tile[(w / nx) * stride + w % nx] = src[w];
-        __syncwarp();
-        if (lane < cnt) {
-            const int64_t L = L0 + lane;
-            const int64_t s = L / (ny * nz);
-            thomas(tile + lane * stride, 1, nx, kk[s], m + (size_t)(3 * s) * nmax, c + (size_t)(3 * s) * nmax);
+        for (int64_t w = threadIdx.x; w < cnt * nx; w += 2 * kLineTile) tile[(w / nx) * stride + w % nx] = src[w];
+        __syncthreads();
+        const int64_t s = (L0 + l) / (ny * nz);
+        double* row = tile + l * stride;
+        const LineEnd end = line_end(row, 1, nx, top);
+        double rp = 0.0;
+        if (l < cnt) {
+            rp = row[p];  // read by both ends before either writes it
+            s_last[threadIdx.x] = end_eliminate(end, kk[s], m + (size_t)(3 * s) * nmax);
         }
-        __syncwarp();
+        __syncthreads();
+        if (l < cnt) {
+            const double up = meet(rp, kk[s], s_last[l], s_last[kLineTile + l], gi[3 * s]);
+            end_back(end, c + (size_t)(3 * s) * nmax, up);
+            if (top) row[p] = up;
+        }
+        __syncthreads();
         double* dst = rho + L0 * nx;
-        for (int64_t w = lane; w < cnt * nx; w += kLineTile) dst[w] = tile[(w / nx) * stride + w % nx];
-        __syncwarp();
+        for (int64_t w = threadIdx.x; w < cnt * nx; w += 2 * kLineTile) dst[w] = tile[(w / nx) * stride + w % nx];
+        __syncthreads();
     }
 }
 
-// x lines longer than a shared-memory tile allows: each thread walks its own line.
+// Lines of n values at rho + base(L), stride apart, two lanes per line: a
+// warp takes lines [L0, L0 + 16), lanes 0-15 their top ends and lanes 16-31
+// their bottom ends (lane pairs l, l + 16 share a line), and the ends meet
+// through one shuffle.  The loop runs per warp, so every lane reaches the
+// shuffle.  base(L) and the coefficient row t(L) come from the functor.
+template <typename Line>
+__device__ __forceinline__ void solve_lines_by_warp(double* __restrict__ rho, int64_t lines, int64_t n,
+                                                    int64_t stride, int64_t nmax, const double* __restrict__ m,
+                                                    const double* __restrict__ c, const double* __restrict__ gi,
+                                                    const double* __restrict__ kk, Line line) {
+    const int lane = threadIdx.x & 31;
+    const bool top = lane < kLinesPerWarp;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t p = n >> 1;
+    for (int64_t L0 = warp * kLinesPerWarp; L0 < lines; L0 += nwarps * kLinesPerWarp) {
+        const int64_t L = L0 + (lane & (kLinesPerWarp - 1));
+        const bool valid = L < lines;
+        int64_t base = 0, s = 0, t = 0;
+        if (valid) line(L, base, s, t);
+        double* row0 = rho + base;
+        const LineEnd end = line_end(row0, stride, n, top);
+        double rp = 0.0, last = 0.0;
+        if (valid) {
+            rp = row0[p * stride];  // read by both ends before either writes it
+            last = end_eliminate(end, kk[s], m + (size_t)t * nmax);
+        }
+        const double other = __shfl_xor_sync(0xFFFFFFFFu, last, kLinesPerWarp);
+        __syncwarp();  // orders the reads of row p above before its write below
+        if (valid) {
+            const double up = meet(rp, kk[s], top ? last : other, top ? other : last, gi[t]);
+            end_back(end, c + (size_t)t * nmax, up);
+            if (top) row0[p * stride] = up;
+        }
+    }
+}
+
+// x lines longer than a shared-memory tile allows: walked in global memory.
 __global__ void k_diff_x_direct(double* __restrict__ rho, int64_t lines, int64_t nx, int64_t ny, int64_t nz,
                                 int64_t nmax, const double* __restrict__ m, const double* __restrict__ c,
-                                const double* __restrict__ kk) {
-    for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < lines;
-         L += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = L / (ny * nz);
-        thomas(rho + L * nx, 1, nx, kk[s], m + (size_t)(3 * s) * nmax, c + (size_t)(3 * s) * nmax);
-    }
+                                const double* __restrict__ gi, const double* __restrict__ kk) {
+    solve_lines_by_warp(rho, lines, nx, 1, nmax, m, c, gi, kk, [&](int64_t L, int64_t& base, int64_t& s, int64_t& t) {
+        s = L / (ny * nz);
+        base = L * nx;
+        t = 3 * s;
+    });
 }
 
-// y lines (axis 1) or z lines (axis 2): thread t = (s, outer, x); consecutive
-// threads are consecutive x, so every step of the recurrence is coalesced.
+// y lines (axis 1) or z lines (axis 2): line L = (s, outer, x), consecutive
+// lines are consecutive x, so every step of the recurrence is coalesced.
 __global__ void k_diff_yz(double* __restrict__ rho, int axis, int32_t S, int64_t nx, int64_t ny, int64_t nz,
                           int64_t nmax, const double* __restrict__ m, const double* __restrict__ c,
-                          const double* __restrict__ kk) {
+                          const double* __restrict__ gi, const double* __restrict__ kk) {
     const int64_t nv = nx * ny * nz;
     const int64_t outer = axis == 1 ? nz : ny;
     const int64_t lines = (int64_t)S * outer * nx;
     const int64_t n = axis == 1 ? ny : nz;
     const int64_t stride = axis == 1 ? nx : nx * ny;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lines; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t x = t % nx;
-        const int64_t r = t / nx;
-        const int64_t o = r % outer;
-        const int64_t s = r / outer;
-        const int64_t base = s * nv + x + (axis == 1 ? o * nx * ny : o * nx);
-        thomas(rho + base, stride, n, kk[s], m + (size_t)(3 * s + axis) * nmax, c + (size_t)(3 * s + axis) * nmax);
-    }
+    solve_lines_by_warp(rho, lines, n, stride, nmax, m, c, gi, kk,
+                        [&](int64_t L, int64_t& base, int64_t& s, int64_t& t) {
+                            const int64_t x = L % nx;
+                            const int64_t r = L / nx;
+                            const int64_t o = r % outer;
+                            s = r / outer;
+                            base = s * nv + x + (axis == 1 ? o * nx * ny : o * nx);
+                            t = 3 * s + axis;
+                        });
 }
 
 __global__ void k_diff_gradient(const double* __restrict__ rho, int32_t S, int64_t nx, int64_t ny, int64_t nz,
@@ -209,6 +314,7 @@ struct mech_diffusion {
     double* d_lam = nullptr;
     double* d_m = nullptr;
     double* d_c = nullptr;
+    double* d_gi = nullptr;
     double* d_k = nullptr;
     std::vector<void*> allocs;
 
@@ -288,6 +394,7 @@ int mech_diffusion_create(mech_diffusion_t** out, int64_t nx, int64_t ny, int64_
     if (rc == MECH_OK) rc = h->alloc(&h->d_lam, (size_t)h->S);
     if (rc == MECH_OK) rc = h->alloc(&h->d_m, (size_t)3 * h->S * h->nmax);
     if (rc == MECH_OK) rc = h->alloc(&h->d_c, (size_t)3 * h->S * h->nmax);
+    if (rc == MECH_OK) rc = h->alloc(&h->d_gi, (size_t)3 * h->S);
     if (rc == MECH_OK) rc = h->alloc(&h->d_k, (size_t)h->S);
     if (rc != MECH_OK) return bail(rc);
     rc = dcuda(cudaMemcpyAsync(h->d_D, D, h->S * 8, cudaMemcpyHostToDevice, h->stream), "upload D");
@@ -296,10 +403,11 @@ int mech_diffusion_create(mech_diffusion_t** out, int64_t nx, int64_t ny, int64_
     if (rc == MECH_OK) rc = dcuda(cudaMemsetAsync(h->d_rho, 0, nvals * 8, h->stream), "zero densities");
     if (rc == MECH_OK) rc = dcuda(cudaStreamSynchronize(h->stream), "create");
     if (rc != MECH_OK) return bail(rc);
-    // the staged x tile needs at most 32 x 191 doubles = 48,896 bytes, within
-    // the default 48 KiB of dynamic shared memory: no per-function attribute
-    // (a process-wide setting) is changed
-    static_assert(kLineTile * kMaxNxTile * sizeof(double) <= 48 * 1024, "x tile within the default limit");
+    // the staged x tile needs at most 32 x 189 doubles = 48,384 bytes, and the
+    // meeting values 512 bytes, within the default 48 KiB of shared memory: no
+    // per-function attribute (a process-wide setting) is changed
+    static_assert((kLineTile * (kMaxNxTile | 1) + 2 * kLineTile) * sizeof(double) <= 48 * 1024,
+                  "x tile and meeting values within the default limit");
     *out = h;
     return MECH_OK;
 }
@@ -344,27 +452,29 @@ int mech_diffusion_step(mech_diffusion_t* h, double dt, int64_t n_steps) {
     if (dt != h->dt_coef) {
         k_diff_coeffs<<<grid_for(3 * h->S, 64, h->sms), 64, 0, h->stream>>>(h->S, h->nx, h->ny, h->nz, h->nmax,
                                                                                h->dx, dt, h->d_D, h->d_lam, h->d_m,
-                                                                               h->d_c, h->d_k);
+                                                                               h->d_c, h->d_gi, h->d_k);
         DTRY(dcuda(cudaGetLastError(), "coefficients"));
         h->dt_coef = dt;
     }
     const int64_t xlines = (int64_t)h->S * h->ny * h->nz;
     const int64_t ylines = (int64_t)h->S * h->nz * h->nx;
     const int64_t zlines = (int64_t)h->S * h->ny * h->nx;
+    // two threads per line everywhere: 32 staged x lines per 64-thread block,
+    // otherwise 16 lines per warp
     const int xblocks = grid_for(xlines, kLineTile, h->sms);
     const int xbytes = (int)(kLineTile * (h->nx | 1) * sizeof(double));
+    const int wblock = 128, lines_per_block = wblock / 32 * kLinesPerWarp;
     for (int64_t step = 0; step < n_steps; ++step) {
         if (h->nx <= kMaxNxTile)
-            k_diff_x_tiled<<<xblocks, kLineTile, xbytes, h->stream>>>(h->d_rho, xlines, h->nx, h->ny, h->nz, h->nmax,
-                                                                      h->d_m, h->d_c, h->d_k);
+            k_diff_x_tiled<<<xblocks, 2 * kLineTile, xbytes, h->stream>>>(h->d_rho, xlines, h->nx, h->ny, h->nz,
+                                                                          h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
         else
-            k_diff_x_direct<<<grid_for(xlines, 128, h->sms), 128, 0, h->stream>>>(h->d_rho, xlines, h->nx, h->ny,
-                                                                                  h->nz, h->nmax, h->d_m, h->d_c,
-                                                                                  h->d_k);
-        k_diff_yz<<<grid_for(ylines, 128, h->sms), 128, 0, h->stream>>>(h->d_rho, 1, h->S, h->nx, h->ny, h->nz,
-                                                                        h->nmax, h->d_m, h->d_c, h->d_k);
-        k_diff_yz<<<grid_for(zlines, 128, h->sms), 128, 0, h->stream>>>(h->d_rho, 2, h->S, h->nx, h->ny, h->nz,
-                                                                        h->nmax, h->d_m, h->d_c, h->d_k);
+            k_diff_x_direct<<<grid_for(xlines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
+                h->d_rho, xlines, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
+        k_diff_yz<<<grid_for(ylines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
+            h->d_rho, 1, h->S, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
+        k_diff_yz<<<grid_for(zlines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
+            h->d_rho, 2, h->S, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
         DTRY(dcuda(cudaGetLastError(), "diffusion step"));
     }
     return MECH_OK;

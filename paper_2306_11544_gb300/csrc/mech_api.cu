@@ -106,6 +106,7 @@ struct mech {
     uint32_t* d_count[2] = {nullptr, nullptr};
     uint32_t* d_start = nullptr;
     uint32_t* d_bsum = nullptr;
+    uint32_t* d_bcount[2] = {nullptr, nullptr};  // cells per scan block, this step and the next
     uint32_t* d_occ = nullptr;
     size_t vcap = 0;  // capacity (entries) of count/start
     double* d_io = nullptr;  // 6n doubles of staging
@@ -204,6 +205,8 @@ struct mech {
         a.tmp = d_tmp;
         a.count_cur = d_count[a_idx];
         a.count_nxt = d_count[a_idx ^ 1];
+        a.bcount_cur = d_bcount[a_idx];
+        a.bcount_nxt = d_bcount[a_idx ^ 1];
         a.start = d_start;
         a.occ = d_occ;
         a.R64 = d_R64;
@@ -317,16 +320,20 @@ int build_grids(mech_t* h) {
         for (int p = 0; p < 2; ++p) h->free_ptr(h->d_count[p], h->vcap * 4);
         h->free_ptr(h->d_start, h->vcap * 4);
         h->free_ptr(h->d_bsum, h->vcap / kScanTile * 4);
+        for (int p = 0; p < 2; ++p) h->free_ptr(h->d_bcount[p], h->vcap / kScanTile * 4);
         h->free_ptr(h->d_occ, (h->vcap / 32 + 1) * 4);
         h->d_count[0] = h->d_count[1] = nullptr;
         h->d_start = nullptr;
         h->d_bsum = nullptr;
+        h->d_bcount[0] = h->d_bcount[1] = nullptr;
         h->d_occ = nullptr;
         h->vcap = 0;
         MECH_TRY(h->alloc(&h->d_count[0], Vpad));
         MECH_TRY(h->alloc(&h->d_count[1], Vpad));
         MECH_TRY(h->alloc(&h->d_start, Vpad));
         MECH_TRY(h->alloc(&h->d_bsum, Vpad / kScanTile));
+        MECH_TRY(h->alloc(&h->d_bcount[0], Vpad / kScanTile));
+        MECH_TRY(h->alloc(&h->d_bcount[1], Vpad / kScanTile));
         MECH_TRY(h->alloc(&h->d_occ, Vpad / 32 + 1));
         h->vcap = Vpad;
     }
@@ -355,6 +362,8 @@ int build_grids(mech_t* h) {
     CUDA_TRY(cudaMemcpyAsync(h->d_grids, g.data(), g.size() * sizeof(GridDev), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[0], Vpad, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_count[1], Vpad, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_bcount[0], Vpad / kScanTile, h->stream));
+    CUDA_TRY(launch_zero_u32(h->d_bcount[1], Vpad / kScanTile, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_occ, Vpad / 32 + 1, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_tcount[0], NT, h->stream));
     CUDA_TRY(launch_zero_u32(h->d_tcount[1], NT, h->stream));
@@ -381,6 +390,7 @@ int ensure_keys(mech_t* h) {
     StepArgs a = h->args(h->cur, 1);
     for (int p = 0; p < 2; ++p) {  // this step's histograms are rebuilt; the next step's start from zero
         CUDA_TRY(launch_zero_u32(h->d_count[p], h->Vpad, h->stream));
+        CUDA_TRY(launch_zero_u32(h->d_bcount[p], h->Vpad / kScanTile, h->stream));
         CUDA_TRY(launch_zero_u32(h->d_tcount[p], h->NT, h->stream));
     }
     CUDA_TRY(launch_keys(a, h->elem_grid, h->stream));
@@ -394,7 +404,11 @@ int enqueue_step(mech_t* h, int integrate, bool profile = false) {
     cudaEvent_t* ev = nullptr;
     if (profile && h->prof_steps < mech::kProfCap) ev = &h->prof_ev[(size_t)h->prof_steps * (mech::kProfPhases + 1)];
     if (ev) CUDA_TRY(cudaEventRecord(ev[0], h->stream));
-    CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, h->d_ndense, h->d_occ, h->stream));
+    // the scan starts from the block sums counted with the histogram (by the
+    // previous step's force epilogue, or by k_keys) and clears the next
+    // step's block sums
+    CUDA_TRY(launch_scan_blocks(a.count_cur, h->Vpad, a.bcount_cur, a.bcount_nxt, h->d_start, h->d_ndense,
+                                h->d_occ, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[1], h->stream));
     CUDA_TRY(launch_scatter(a, h->elem_grid, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[2], h->stream));

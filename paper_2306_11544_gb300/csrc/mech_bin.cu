@@ -41,6 +41,7 @@ __global__ void k_keys(const StepArgs a) {
             tile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
         warp_add(a.count_cur, key, valid);
+        warp_add(a.bcount_cur, key / (uint32_t)kScanTile, valid);
         warp_add(a.tcount_cur, tile, valid);
         if (valid) a.key[i] = key;
     }
@@ -110,12 +111,15 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ bsum, 
 }
 
 // start[v] = sum_{u<v} count[u]; each thread owns 16 consecutive voxels, and
-// writes their occupancy bits.
+// writes their occupancy bits.  zero_blocks (may be null): the block's entry
+// of another block-sum array is cleared.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ count,
                                                             const uint32_t* __restrict__ boff,
                                                             uint32_t* __restrict__ start,
-                                                            uint16_t* __restrict__ occ16) {
+                                                            uint16_t* __restrict__ occ16,
+                                                            uint32_t* __restrict__ zero_blocks) {
     __shared__ uint32_t sh[33];
+    if (zero_blocks && threadIdx.x == 0) zero_blocks[blockIdx.x] = 0u;
     const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
     const uint4* c4 = reinterpret_cast<const uint4*>(count + base);
     uint4 q[kScanItems / 4];
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // Step 1c: every cell goes to start[key] + slot, carrying (id, A index).  The
 // slot is taken by counting the voxel's histogram entry back down, which
 // leaves the histogram zero for its reuse as the next step's accumulator; the
-// slot order inside a voxel comes from the atomics and k_canon_rank makes it
+// slot order inside a voxel comes from the atomics and k_canon makes it
 // canonical.
 __global__ void k_scatter(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -169,11 +173,19 @@ __global__ void k_scatter(const StepArgs a) {
     }
 }
 
-// Step 1d: rank each cell inside its voxel by caller index (ids are unique),
-// giving its final voxel-order position f; record perm[f] (its A index), its
-// key and its id.
-__global__ void k_canon_rank(const StepArgs a) {
+// Step 1d: canonicalisation, one thread per scattered entry q.  The cell is
+// ranked inside its voxel by caller index (ids are unique), which gives its
+// final voxel-order position f; perm[f] (its A index), its key and its id are
+// recorded, and its force record is gathered from its A position and written
+// at f (position relative to the grid centre as hi on the q grid + 16-bit
+// residual, radius, coefficient square roots).  The rest of the state
+// (position, compensation, previous velocity) stays in A order: the force
+// kernels read it at perm[f] for the AB2 update and write the new state at f.
+// Cells that stay in their voxel keep their relative order, so both the reads
+// at perm[f] and the writes at f are close to sequential.
+__global__ void k_canon(const StepArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
+    const size_t np = a.npad;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const unsigned long long e = a.tmp[q];
         const uint32_t id = (uint32_t)(e >> 32);
@@ -194,25 +206,6 @@ __global__ void k_canon_rank(const StepArgs a) {
         a.perm[f] = src;
         a.vkey_s[f] = k;
         a.B.id[f] = id;  // written here, so the next state's slot map is complete even if a force kernel aborts
-    }
-}
-
-// Step 1e: in voxel order f, gather each cell from its A position and write its
-// force record (position relative to the grid centre as hi on the q grid +
-// 16-bit residual, radius, coefficient square roots).  The rest of the state
-// (position, compensation, previous velocity) stays in A order: the force
-// kernels read it at perm[f] for the AB2 update and write the new state at f.
-// Cells that stay in their voxel keep their relative order, so both the reads
-// at perm[f] and the writes at f are close to sequential.
-__global__ void k_canon_gather(const StepArgs a) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const size_t np = a.npad;
-    for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < a.n; f += stride) {
-        const uint32_t src = a.perm[f];
-        if (src >= a.n) {  // only after an earlier device error
-            atomicOr(a.err, kErrIndex);
-            continue;
-        }
         const int r = rep_of_cell(a.grids, a.nrep, f);
         const GridDev& g = a.grids[r];
         float hi[3], lo[3];
@@ -564,7 +557,15 @@ cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, ui
     const uint32_t nb = vpad / kScanTile;
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(count, bsum);
     k_scan_top<<<1, 1024, 0, s>>>(bsum, nb, zero_word);
-    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, reinterpret_cast<uint16_t*>(occ));
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, reinterpret_cast<uint16_t*>(occ), nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_blocks(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* zero_blocks,
+                               uint32_t* start, uint32_t* zero_word, uint32_t* occ, cudaStream_t s) {
+    const uint32_t nb = vpad / kScanTile;
+    k_scan_top<<<1, 1024, 0, s>>>(bsum, nb, zero_word);
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(count, bsum, start, reinterpret_cast<uint16_t*>(occ), zero_blocks);
     return cudaGetLastError();
 }
 
@@ -576,8 +577,7 @@ cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    k_canon_rank<<<grid, 256, 0, s>>>(a);
-    k_canon_gather<<<grid, 256, 0, s>>>(a);
+    k_canon<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

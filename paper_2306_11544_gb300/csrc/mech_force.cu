@@ -310,10 +310,12 @@ __device__ __forceinline__ uint32_t ab2_epilogue(const StepArgs& a, const GridDe
     return ab2_apply<MODE>(a, g, q, st, ax, ay, az, Rf, Rlo, nix, niy, niz);
 }
 
-// Next-step histograms (voxels, tiles) and key of cell q; all 32 lanes call it.
+// Next-step histograms (voxels, scan blocks, tiles) and key of cell q; all 32
+// lanes call it.
 __device__ __forceinline__ void next_step_counts(const StepArgs& a, uint32_t q, uint32_t nkey, uint32_t ntile,
                                                  bool valid) {
     warp_add(a.tcount_nxt, ntile, valid);  // many lanes share a tile: aggregate
+    warp_add(a.bcount_nxt, nkey / (uint32_t)kScanTile, valid);  // and a scan block
     if (valid) {
         atomicAdd(&a.count_nxt[nkey], 1u);  // voxels hold ~2 cells: plain reduction
         a.key[q] = nkey;

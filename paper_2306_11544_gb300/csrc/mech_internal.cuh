@@ -33,7 +33,9 @@
 //     count[2][Vpad] (histograms of this and the next step; the scatter
 //     counts this step's histogram back down to zero), start[Vpad] (exclusive
 //     scan of count: cells of voxel v are the sorted positions start[v] ..
-//     start[v+1]-1), occ[Vpad/32 + 1] (bit v: count > 0).
+//     start[v+1]-1), occ[Vpad/32 + 1] (bit v: count > 0), bcount[2][Vpad /
+//     8192] (cells of each scan block of 8,192 voxels, counted with the
+//     histograms, so a step's scan starts from the block sums).
 //   * voxel tiles: the grid is cut into blocks of TX x TY x TZ voxels (powers
 //     of two); tcount[2][T] counts the cells of each tile (this step, next
 //     step), tdense[T] flags the tiles processed by the shared-memory tile
@@ -183,6 +185,8 @@ struct StepArgs {
     unsigned long long* tmp;
     uint32_t* count_cur;
     uint32_t* count_nxt;
+    uint32_t* bcount_cur;  // cells per scan block (kScanTile voxels), this step and the next
+    uint32_t* bcount_nxt;
     uint32_t* start;
     uint32_t* occ;         // 1 bit per voxel: count > 0 (written by the scan)
     const double* R64;    // FP64 parameters in caller order (FP64 mode)
@@ -233,6 +237,11 @@ cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
 cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start,
                         uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
+// The same scan when bsum already holds the cells of each block of kScanTile
+// voxels (counted with the histogram): no reduce pass; zero_blocks (the next
+// step's block sums) is cleared on the way.
+cudaError_t launch_scan_blocks(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* zero_blocks,
+                               uint32_t* start, uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
 cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);

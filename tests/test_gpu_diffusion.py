@@ -1,5 +1,5 @@
 """Substrate diffusion on the GPU against the diffusion oracle, for grids
-whose x lines are staged in shared memory (nx <= 191) and grids whose x lines
+whose x lines are staged in shared memory (nx <= 189) and grids whose x lines
 are walked in global memory, several substrates, changing dt, and one-voxel
 axes.
 
