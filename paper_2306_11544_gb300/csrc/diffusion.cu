@@ -15,11 +15,10 @@
 //   lines of an axis and the pivots inverted once:
 //      m_0 = T_00;  m_i = T_ii + k c_{i-1} (i >= 1);  w_i = 1 / m_i;
 //      c_i = -k w_i
-//   (no division inside the recurrences: an FP64 division costs about six
-//   FP64 additions on this GPU), in its two-ended form: the matrix reads the
-//   same from either end (T_ii = T_{n-1-i,n-1-i}), so eliminating upward from
-//   the last row produces the same pivots in mirror order, bit for bit.  With
-//   p = floor(n / 2):
+//   (no division inside the recurrences), in its two-ended form: the matrix
+//   reads the same from either end (T_ii = T_{n-1-i,n-1-i}), so eliminating
+//   upward from the last row produces the same pivots in mirror order, bit
+//   for bit.  With p = floor(n / 2):
 //      top    y_0 = old_0 w_0;  y_i = (old_i + k y_{i-1}) w_i        (i < p)
 //      bottom z_{n-1} = old_{n-1} w_0;
 //             z_i = (old_i + k z_{i+1}) w_{n-1-i}                  (i > p)
@@ -30,10 +29,13 @@
 //             u_i = z_i - c_{n-1-i} u_{i-1} (i = p+1 .. n-1)
 //   The solution is that of the one-ended elimination up to rounding, and a
 //   line's dependent chain is n steps instead of 2 n: two threads share a
-//   line, one per end.  FP64 with IEEE operations in this order (no
-//   contraction), so every value is reproducible run to run.  Gradients:
-//   central differences inside, one-sided at the faces, zero along an axis of
-//   one voxel; array [s][axis][v].
+//   line, one per end.  Arithmetic: FP64, each a + b c above one fused
+//   multiply-add (three FP64 operations per value and solve: this GPU's FP64
+//   pipe runs at about 1/60 of its FP32 rate, and it, not memory, bounds the
+//   solver), IEEE operations in a fixed order, so every value is
+//   reproducible run to run.  Gradients: central differences inside,
+//   one-sided at the faces, zero along an axis of one voxel; array
+//   [s][axis][v].
 //
 // GB300 mapping: the work is a set of independent recurrences (one per end
 // of a grid line), so every kernel runs two threads per line.  Lines along y
@@ -133,7 +135,7 @@ __device__ __forceinline__ double end_eliminate(const LineEnd& L, double k, cons
     double prev = 0.0;
     for (int64_t j = 0; j < L.cnt; ++j) {
         const double r = L.base[j * L.step];
-        prev = j == 0 ? __dmul_rn(r, w[0]) : __dmul_rn(__dadd_rn(r, __dmul_rn(k, prev)), w[j]);
+        prev = j == 0 ? __dmul_rn(r, w[0]) : __dmul_rn(__fma_rn(k, prev, r), w[j]);
         L.base[j * L.step] = prev;
     }
     return prev;
@@ -141,17 +143,55 @@ __device__ __forceinline__ double end_eliminate(const LineEnd& L, double k, cons
 
 // Value of the meeting row from its right-hand side and the two ends' last values.
 __device__ __forceinline__ double meet(double rp, double k, double y, double z, double gi) {
-    return __dmul_rn(__dadd_rn(__dadd_rn(rp, __dmul_rn(k, y)), __dmul_rn(k, z)), gi);
+    return __dmul_rn(__fma_rn(k, z, __fma_rn(k, y, rp)), gi);
 }
 
 // Back substitution from the meeting row out to the end's extremity.
 __device__ __forceinline__ void end_back(const LineEnd& L, const double* __restrict__ c, double up) {
     double next = up;
     for (int64_t j = L.cnt - 1; j >= 0; --j) {
-        next = __dsub_rn(L.base[j * L.step], __dmul_rn(c[j], next));
+        next = __fma_rn(-c[j], next, L.base[j * L.step]);
         L.base[j * L.step] = next;
     }
 }
+
+// The same two recurrences with the whole end in registers (cnt <= MAXC):
+// all its values are loaded in one round before the elimination starts (the
+// loop above waits for every load in turn), only the solution is stored.
+template <int MAXC>
+__device__ __forceinline__ double regs_eliminate(const LineEnd& L, double k, const double* __restrict__ w,
+                                                 double (&v)[MAXC]) {
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j)
+        if (j < L.cnt) v[j] = L.base[j * L.step];
+    double prev = 0.0;
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j)
+        if (j < L.cnt) {
+            prev = j == 0 ? __dmul_rn(v[0], w[0]) : __dmul_rn(__fma_rn(k, prev, v[j]), w[j]);
+            v[j] = prev;
+        }
+    return prev;
+}
+
+template <int MAXC>
+__device__ __forceinline__ void regs_back(const LineEnd& L, const double* __restrict__ c, double up,
+                                          double (&v)[MAXC]) {
+    double next = up;
+#pragma unroll
+    for (int j = MAXC - 1; j >= 0; --j)
+        if (j < L.cnt) {
+            next = __fma_rn(-c[j], next, v[j]);
+            v[j] = next;
+        }
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j)
+        if (j < L.cnt) L.base[j * L.step] = v[j];
+}
+
+// Register capacity for a line of n values: each end holds at most n / 2.
+constexpr int kRegsSmall = 16, kRegsLarge = 40;
+inline int regs_for(int64_t n) { return n <= 2 * kRegsSmall + 1 ? kRegsSmall : (n <= 2 * kRegsLarge + 1 ? kRegsLarge : 0); }
 
 // x lines: line L = (s nz + z) ny + y occupies rho[L nx, (L + 1) nx).  A
 // block stages lines [L0, L0 + 32) (one contiguous run) in shared memory;
@@ -159,6 +199,7 @@ __device__ __forceinline__ void end_back(const LineEnd& L, const double* __restr
 // ends meet through shared memory, and the block writes the lines back.  The
 // shared row stride is odd (in doubles), so the 16 lanes of a half-warp hit
 // 16 different banks.
+template <int MAXC>
 __global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
                                                                int64_t ny, int64_t nz, int64_t nmax,
                                                                const double* __restrict__ m,
@@ -180,14 +221,19 @@ __global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restri
         double* row = tile + l * stride;
         const LineEnd end = line_end(row, 1, nx, top);
         double rp = 0.0;
+        double v[MAXC > 0 ? MAXC : 1];
         if (l < cnt) {
             rp = row[p];  // read by both ends before either writes it
-            s_last[threadIdx.x] = end_eliminate(end, kk[s], m + (size_t)(3 * s) * nmax);
+            const double* w = m + (size_t)(3 * s) * nmax;
+            if constexpr (MAXC > 0) s_last[threadIdx.x] = regs_eliminate<MAXC>(end, kk[s], w, v);
+            else s_last[threadIdx.x] = end_eliminate(end, kk[s], w);
         }
         __syncthreads();
         if (l < cnt) {
             const double up = meet(rp, kk[s], s_last[l], s_last[kLineTile + l], gi[3 * s]);
-            end_back(end, c + (size_t)(3 * s) * nmax, up);
+            const double* cc = c + (size_t)(3 * s) * nmax;
+            if constexpr (MAXC > 0) regs_back<MAXC>(end, cc, up, v);
+            else end_back(end, cc, up);
             if (top) row[p] = up;
         }
         __syncthreads();
@@ -202,7 +248,7 @@ __global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restri
 // their bottom ends (lane pairs l, l + 16 share a line), and the ends meet
 // through one shuffle.  The loop runs per warp, so every lane reaches the
 // shuffle.  base(L) and the coefficient row t(L) come from the functor.
-template <typename Line>
+template <int MAXC, typename Line>
 __device__ __forceinline__ void solve_lines_by_warp(double* __restrict__ rho, int64_t lines, int64_t n,
                                                     int64_t stride, int64_t nmax, const double* __restrict__ m,
                                                     const double* __restrict__ c, const double* __restrict__ gi,
@@ -220,33 +266,39 @@ __device__ __forceinline__ void solve_lines_by_warp(double* __restrict__ rho, in
         double* row0 = rho + base;
         const LineEnd end = line_end(row0, stride, n, top);
         double rp = 0.0, last = 0.0;
+        double v[MAXC > 0 ? MAXC : 1];
         if (valid) {
             rp = row0[p * stride];  // read by both ends before either writes it
-            last = end_eliminate(end, kk[s], m + (size_t)t * nmax);
+            if constexpr (MAXC > 0) last = regs_eliminate<MAXC>(end, kk[s], m + (size_t)t * nmax, v);
+            else last = end_eliminate(end, kk[s], m + (size_t)t * nmax);
         }
         const double other = __shfl_xor_sync(0xFFFFFFFFu, last, kLinesPerWarp);
         __syncwarp();  // orders the reads of row p above before its write below
         if (valid) {
             const double up = meet(rp, kk[s], top ? last : other, top ? other : last, gi[t]);
-            end_back(end, c + (size_t)t * nmax, up);
+            if constexpr (MAXC > 0) regs_back<MAXC>(end, c + (size_t)t * nmax, up, v);
+            else end_back(end, c + (size_t)t * nmax, up);
             if (top) row0[p * stride] = up;
         }
     }
 }
 
-// x lines longer than a shared-memory tile allows: walked in global memory.
+// x lines longer than a shared-memory tile allows (and than the register
+// form holds): walked in global memory.
 __global__ void k_diff_x_direct(double* __restrict__ rho, int64_t lines, int64_t nx, int64_t ny, int64_t nz,
                                 int64_t nmax, const double* __restrict__ m, const double* __restrict__ c,
                                 const double* __restrict__ gi, const double* __restrict__ kk) {
-    solve_lines_by_warp(rho, lines, nx, 1, nmax, m, c, gi, kk, [&](int64_t L, int64_t& base, int64_t& s, int64_t& t) {
-        s = L / (ny * nz);
-        base = L * nx;
-        t = 3 * s;
-    });
+    solve_lines_by_warp<0>(rho, lines, nx, 1, nmax, m, c, gi, kk,
+                           [&](int64_t L, int64_t& base, int64_t& s, int64_t& t) {
+                               s = L / (ny * nz);
+                               base = L * nx;
+                               t = 3 * s;
+                           });
 }
 
 // y lines (axis 1) or z lines (axis 2): line L = (s, outer, x), consecutive
 // lines are consecutive x, so every step of the recurrence is coalesced.
+template <int MAXC>
 __global__ void k_diff_yz(double* __restrict__ rho, int axis, int32_t S, int64_t nx, int64_t ny, int64_t nz,
                           int64_t nmax, const double* __restrict__ m, const double* __restrict__ c,
                           const double* __restrict__ gi, const double* __restrict__ kk) {
@@ -255,7 +307,7 @@ __global__ void k_diff_yz(double* __restrict__ rho, int axis, int32_t S, int64_t
     const int64_t lines = (int64_t)S * outer * nx;
     const int64_t n = axis == 1 ? ny : nz;
     const int64_t stride = axis == 1 ? nx : nx * ny;
-    solve_lines_by_warp(rho, lines, n, stride, nmax, m, c, gi, kk,
+    solve_lines_by_warp<MAXC>(rho, lines, n, stride, nmax, m, c, gi, kk,
                         [&](int64_t L, int64_t& base, int64_t& s, int64_t& t) {
                             const int64_t x = L % nx;
                             const int64_t r = L / nx;
@@ -464,17 +516,23 @@ int mech_diffusion_step(mech_diffusion_t* h, double dt, int64_t n_steps) {
     const int xblocks = grid_for(xlines, kLineTile, h->sms);
     const int xbytes = (int)(kLineTile * (h->nx | 1) * sizeof(double));
     const int wblock = 128, lines_per_block = wblock / 32 * kLinesPerWarp;
+    const int rx = regs_for(h->nx), ry = regs_for(h->ny), rz = regs_for(h->nz);
     for (int64_t step = 0; step < n_steps; ++step) {
-        if (h->nx <= kMaxNxTile)
-            k_diff_x_tiled<<<xblocks, 2 * kLineTile, xbytes, h->stream>>>(h->d_rho, xlines, h->nx, h->ny, h->nz,
-                                                                          h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
-        else
+        if (h->nx <= kMaxNxTile) {
+            auto kx = rx == kRegsSmall ? k_diff_x_tiled<kRegsSmall>
+                                       : (rx == kRegsLarge ? k_diff_x_tiled<kRegsLarge> : k_diff_x_tiled<0>);
+            kx<<<xblocks, 2 * kLineTile, xbytes, h->stream>>>(h->d_rho, xlines, h->nx, h->ny, h->nz, h->nmax,
+                                                              h->d_m, h->d_c, h->d_gi, h->d_k);
+        } else {
             k_diff_x_direct<<<grid_for(xlines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
                 h->d_rho, xlines, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
-        k_diff_yz<<<grid_for(ylines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
-            h->d_rho, 1, h->S, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
-        k_diff_yz<<<grid_for(zlines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
-            h->d_rho, 2, h->S, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
+        }
+        for (int axis = 1; axis <= 2; ++axis) {
+            const int r = axis == 1 ? ry : rz;
+            auto ky = r == kRegsSmall ? k_diff_yz<kRegsSmall> : (r == kRegsLarge ? k_diff_yz<kRegsLarge> : k_diff_yz<0>);
+            ky<<<grid_for(axis == 1 ? ylines : zlines, lines_per_block, h->sms), wblock, 0, h->stream>>>(
+                h->d_rho, axis, h->S, h->nx, h->ny, h->nz, h->nmax, h->d_m, h->d_c, h->d_gi, h->d_k);
+        }
         DTRY(dcuda(cudaGetLastError(), "diffusion step"));
     }
     return MECH_OK;

@@ -3,8 +3,10 @@ whose x lines are staged in shared memory (nx <= 189) and grids whose x lines
 are walked in global memory, several substrates, changing dt, and one-voxel
 axes.
 
-Tolerance.  The oracle divides by each Thomas pivot; the kernels multiply by
-the pivot's reciprocal, rounded once.  Each forward step of a line therefore
+Tolerance.  The oracle eliminates each line from its first row, dividing by
+each Thomas pivot; the kernels eliminate from both ends toward the middle row
+(the same pivots, mirrored), multiply by the pivots' reciprocals, rounded
+once, and fuse each multiply-add.  Each step of a recurrence therefore
 differs by at most about two units in the last place (u = 2^-53) of its
 value.  For these systems (k = D dt / dx^2 <= 0.002) every pivot is within
 1 % of 1 + 2k + e and both recurrences contract (|k / m_i|, |c_i| < 0.01), so
