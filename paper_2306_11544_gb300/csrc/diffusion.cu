@@ -200,7 +200,7 @@ inline int regs_for(int64_t n) { return n <= 2 * kRegsSmall + 1 ? kRegsSmall : (
 // shared row stride is odd (in doubles), so the 16 lanes of a half-warp hit
 // 16 different banks.
 template <int MAXC>
-__global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
+__global__ void __launch_bounds__(2 * kLineTile, 6) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
                                                                int64_t ny, int64_t nz, int64_t nmax,
                                                                const double* __restrict__ m,
                                                                const double* __restrict__ c,
@@ -212,10 +212,30 @@ __global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restri
     const int l = threadIdx.x & (kLineTile - 1);
     const bool top = threadIdx.x < kLineTile;
     const int64_t p = nx >> 1;
+    // element w of a staged run is (line w / nx, column w % nx), tile slot
+    // line * stride + column; a run holds at most 32 x 189 values, so the
+    // copies use 32-bit indices advanced by 64 = dr lines + dc columns
+    // without a division
+    const uint32_t n32 = (uint32_t)nx, st32 = (uint32_t)stride;
+    const uint32_t dr = (2u * kLineTile) / n32, dc = (2u * kLineTile) - dr * n32;
+    const uint32_t r0 = threadIdx.x / n32, c0 = threadIdx.x - r0 * n32;
+    auto copy = [&](double* run, bool to_tile, uint32_t W) {
+        uint32_t r = r0, col = c0;
+        for (uint32_t w = threadIdx.x; w < W; w += 2u * kLineTile) {
+            if (to_tile) tile[r * st32 + col] = run[w];
+            else run[w] = tile[r * st32 + col];
+            r += dr;
+            col += dc;
+            if (col >= n32) {
+                col -= n32;
+                ++r;
+            }
+        }
+    };
     for (int64_t L0 = (int64_t)blockIdx.x * kLineTile; L0 < lines; L0 += (int64_t)gridDim.x * kLineTile) {
         const int64_t cnt = lines - L0 < kLineTile ? lines - L0 : kLineTile;
-        const double* src = rho + L0 * nx;
-        for (int64_t w = threadIdx.x; w < cnt * nx; w += 2 * kLineTile) tile[(w / nx) * stride + w % nx] = src[w];
+        const uint32_t W = (uint32_t)(cnt * nx);
+        copy(rho + L0 * nx, true, W);
         __syncthreads();
         const int64_t s = (L0 + l) / (ny * nz);
         double* row = tile + l * stride;
@@ -237,8 +257,7 @@ __global__ void __launch_bounds__(2 * kLineTile) k_diff_x_tiled(double* __restri
             if (top) row[p] = up;
         }
         __syncthreads();
-        double* dst = rho + L0 * nx;
-        for (int64_t w = threadIdx.x; w < cnt * nx; w += 2 * kLineTile) dst[w] = tile[(w / nx) * stride + w % nx];
+        copy(rho + L0 * nx, false, W);
         __syncthreads();
     }
 }
