@@ -766,32 +766,71 @@ __global__ void __launch_bounds__(kVoxWarps * 32, kVoxMinBlocks) k_force_vox(con
 // of every cell whose tile is not dense, in runs of a warp's 32 consecutive
 // cells, and whether the cell is alone in its voxel (its sorted neighbours
 // q - 1 and q + 1 have other keys).
-__global__ void k_sparse_list(const StepArgs a) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+// A block takes 4 x 256 cells per round, each thread 4 cells 256 apart, so the
+// loads of a round (keys, then tile flags) are issued together: the kernel
+// waits on memory, and a thread's rounds are sequential.  One atomic per
+// round reserves the block's list entries (one counter serves the whole grid).
+constexpr int kListBlock = 256, kListPer = 4;
+
+__global__ void __launch_bounds__(kListBlock) k_sparse_list(const StepArgs a) {
+    __shared__ uint32_t s_cnt[kListPer][kListBlock / 32];
+    __shared__ uint32_t s_base;
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     constexpr uint32_t kNone = 0xFFFFFFFFu;  // above every voxel key
-    for (uint32_t base = warp * 32u; base < a.n; base += nwarps * 32u) {
-        const uint32_t q = base + lane;
-        bool sparse = false;
-        uint32_t k = 0;
-        if (q < a.n) {
-            const int r = rep_of_cell(a.grids, a.nrep, q);
-            const GridDev& g = a.grids[r];
-            k = a.vkey_s[q];
-            const Cell3 c = decode(k, g);
-            sparse = !a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)];
+    constexpr uint32_t kRound = kListBlock * kListPer;
+    for (uint32_t base = blockIdx.x * kRound; base < a.n; base += gridDim.x * kRound) {
+        uint32_t k[kListPer], kp[kListPer], kn[kListPer];
+        bool sparse[kListPer];
+#pragma unroll
+        for (int j = 0; j < kListPer; ++j) {
+            const uint32_t q = base + (uint32_t)j * kListBlock + threadIdx.x;
+            const bool last = lane == 31u || q + 1u >= a.n;  // next cell not in this warp's registers
+            k[j] = q < a.n ? a.vkey_s[q] : 0u;
+            kp[j] = (lane == 0u && q > 0u && q < a.n) ? a.vkey_s[q - 1u] : kNone;
+            kn[j] = (last && q + 1u < a.n) ? a.vkey_s[q + 1u] : kNone;
         }
-        uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, k, 1);
-        uint32_t kn = __shfl_down_sync(0xFFFFFFFFu, k, 1);
-        if (lane == 0) kp = (q > 0u && q < a.n) ? a.vkey_s[q - 1u] : kNone;
-        if (lane == 31u || q + 1u >= a.n) kn = q + 1u < a.n ? a.vkey_s[q + 1u] : kNone;
-        const uint32_t alone = (kp != k && kn != k) ? 0x80000000u : 0u;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, sparse);
-        uint32_t off = 0;
-        if (lane == 0 && m) off = atomicAdd(a.nsparse, (uint32_t)__popc(m));
-        off = __shfl_sync(0xFFFFFFFFu, off, 0);
-        if (sparse) a.slist[off + __popc(m & lanemask_lt())] = make_uint2(q | alone, k);
+#pragma unroll
+        for (int j = 0; j < kListPer; ++j) {
+            const uint32_t q = base + (uint32_t)j * kListBlock + threadIdx.x;
+            sparse[j] = false;
+            if (q < a.n) {
+                const int r = rep_of_cell(a.grids, a.nrep, q);
+                const GridDev& g = a.grids[r];
+                const Cell3 c = decode(k[j], g);
+                sparse[j] = !a.tdense[tile_index(g, c.ix, c.iy, c.iz, a.ltx, a.lty, a.ltz)];
+            }
+        }
+        uint32_t m[kListPer];
+#pragma unroll
+        for (int j = 0; j < kListPer; ++j) {
+            const uint32_t q = base + (uint32_t)j * kListBlock + threadIdx.x;
+            const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, k[j], 1);
+            const uint32_t dn = __shfl_down_sync(0xFFFFFFFFu, k[j], 1);
+            if (lane != 0u) kp[j] = up;
+            if (!(lane == 31u || q + 1u >= a.n)) kn[j] = dn;
+            m[j] = __ballot_sync(0xFFFFFFFFu, sparse[j]);
+            if (lane == 0u) s_cnt[j][wib] = (uint32_t)__popc(m[j]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {  // offsets of the (round part, warp) groups, and the block's reservation
+            uint32_t t = 0;
+            for (int j = 0; j < kListPer; ++j)
+                for (int w = 0; w < kListBlock / 32; ++w) {
+                    const uint32_t c = s_cnt[j][w];
+                    s_cnt[j][w] = t;
+                    t += c;
+                }
+            s_base = t ? atomicAdd(a.nsparse, t) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kListPer; ++j)
+            if (sparse[j]) {
+                const uint32_t q = base + (uint32_t)j * kListBlock + threadIdx.x;
+                const uint32_t alone = (kp[j] != k[j] && kn[j] != k[j]) ? 0x80000000u : 0u;
+                a.slist[s_base + s_cnt[j][wib] + __popc(m[j] & lanemask_lt())] = make_uint2(q | alone, k[j]);
+            }
+        __syncthreads();  // s_cnt and s_base are rewritten by the next round
     }
 }
 
@@ -1317,7 +1356,7 @@ cudaError_t launch_force_tiles(const StepArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_sparse_list(const StepArgs& a, int grid, cudaStream_t s) {
     if (a.n == 0 || !a.use_tiles || a.mode == kFP64) return cudaSuccess;
-    k_sparse_list<<<grid, 256, 0, s>>>(a);
+    k_sparse_list<<<grid, kListBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
