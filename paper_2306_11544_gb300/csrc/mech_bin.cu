@@ -159,17 +159,35 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // leaves the histogram zero for its reuse as the next step's accumulator; the
 // slot order inside a voxel comes from the atomics and k_canon makes it
 // canonical.
-__global__ void k_scatter(const StepArgs a) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const uint32_t k = a.key[i];
-        const uint32_t left = atomicSub(&a.count_cur[k], 1u);  // cells of voxel k not yet placed
-        const uint32_t dst = a.start[k] + left - 1u;
-        if (left == 0u || dst >= a.n) {  // only after an earlier device error left the keys inconsistent
-            atomicOr(a.err, kErrIndex);
-            continue;
+__global__ void __launch_bounds__(256) k_scatter(const StepArgs a) {
+    // four cells per thread (256 apart) per round: their key loads, then their
+    // atomics and start[] loads, are issued together
+    constexpr uint32_t kPer = 4, kRound = 256u * kPer;
+    for (uint32_t base = blockIdx.x * kRound; base < a.n; base += gridDim.x * kRound) {
+        uint32_t k[kPer], id[kPer], left[kPer], st[kPer];
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; ++j) {
+            const uint32_t i = base + j * 256u + threadIdx.x;
+            k[j] = i < a.n ? a.key[i] : 0u;
+            id[j] = i < a.n ? a.A.id[i] : 0u;
         }
-        a.tmp[dst] = ((unsigned long long)a.A.id[i] << 32) | (unsigned long long)i;
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; ++j) {
+            const uint32_t i = base + j * 256u + threadIdx.x;
+            left[j] = i < a.n ? atomicSub(&a.count_cur[k[j]], 1u) : 0u;  // cells of voxel k not yet placed
+            st[j] = i < a.n ? a.start[k[j]] : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; ++j) {
+            const uint32_t i = base + j * 256u + threadIdx.x;
+            if (i >= a.n) continue;
+            const uint32_t dst = st[j] + left[j] - 1u;
+            if (left[j] == 0u || dst >= a.n) {  // only after an earlier device error left the keys inconsistent
+                atomicOr(a.err, kErrIndex);
+                continue;
+            }
+            a.tmp[dst] = ((unsigned long long)id[j] << 32) | (unsigned long long)i;
+        }
     }
 }
 
@@ -194,6 +212,21 @@ __global__ void k_canon(const StepArgs a) {
             atomicOr(a.err, kErrIndex);
             continue;
         }
+        // the cell's state at src is loaded before the ranking, whose loads it
+        // does not depend on
+        float xs[3] = {0.f, 0.f, 0.f}, cs[3] = {0.f, 0.f, 0.f};
+        double xd[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (a.mode == kMixedKahan) {
+                xs[d] = a.A.posf[d * np + src];
+                cs[d] = a.A.comp[d * np + src];
+            } else {
+                xd[d] = a.A.pos64[d * np + src];
+            }
+        }
+        const float4 pa = a.A.rec[2 * (size_t)src];
+        const float4 qa = a.A.rec[2 * (size_t)src + 1];
         const uint32_t k = a.key[src];
         const uint32_t s = a.start[k], en = a.start[k + 1];
         uint32_t rank = 0;
@@ -212,8 +245,8 @@ __global__ void k_canon(const StepArgs a) {
         if (a.mode == kMixedKahan) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const float xh = a.A.posf[d * np + src];
-                const float c = a.A.comp[d * np + src];
+                const float xh = xs[d];
+                const float c = cs[d];
                 // value - centre = (x_hi - oc_hi) - (oc_lo + c), both sums error-free
                 float e1, e2;
                 const float s1 = two_sum(xh, -g.oc_hi[d], e1);
@@ -224,7 +257,7 @@ __global__ void k_canon(const StepArgs a) {
         } else {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double x = a.A.pos64[d * np + src];
+                const double x = xd[d];
                 const double rr = __dsub_rn(x, g.oc[d]);
                 const double t = rint(__dmul_rn(rr, (double)g.inv_q));
                 if (fabs(t) < 8388608.0) {
@@ -238,8 +271,6 @@ __global__ void k_canon(const StepArgs a) {
             }
         }
         // radius, its residual and the coefficients travel with the record
-        const float4 pa = a.A.rec[2 * (size_t)src];
-        const float4 qa = a.A.rec[2 * (size_t)src + 1];
         const uint32_t wxy = fix16(lo[0] * g.inv_q) | (fix16(lo[1] * g.inv_q) << 16);
         const uint32_t wzr = fix16(lo[2] * g.inv_q) | (__float_as_uint(qa.w) & 0xFFFF0000u);
         a.B.rec[2 * (size_t)f] = make_float4(hi[0], hi[1], hi[2], pa.w);
