@@ -395,22 +395,23 @@ __global__ void __launch_bounds__(kCellBlock, 4) k_force_cells(const StepArgs a)
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t total = a.use_tiles ? a.nsparse[0] : a.n;
+    // the list entry (or key) of the next iteration is loaded one iteration
+    // ahead, so an iteration's chain of dependent loads starts one step later
+    auto entry = [&](uint32_t idx) -> uint2 {
+        if (idx >= total) return make_uint2(0u, 0u);
+        return a.use_tiles ? a.slist[idx] : make_uint2(idx, a.vkey_s[idx]);
+    };
+    uint2 next = entry(warp * 32u + lane);
     for (uint32_t base = warp * 32u; base < total; base += nwarps * 32u) {
         const uint32_t idx = base + lane;
         const bool valid = idx < total;
+        const uint2 e = next;
+        next = entry(idx + nwarps * 32u);
         uint32_t q = 0, nkey = 0, ntile = 0;
         if (valid) {
-            uint32_t key;
-            bool alone = false;
-            if (a.use_tiles) {
-                const uint2 e = a.slist[idx];
-                q = e.x & 0x7FFFFFFFu;
-                alone = (e.x >> 31) != 0u;
-                key = e.y;
-            } else {
-                q = idx;
-                key = a.vkey_s[q];
-            }
+            q = e.x & 0x7FFFFFFFu;
+            const bool alone = (e.x >> 31) != 0u;  // only set in list entries
+            const uint32_t key = e.y;
             const CellState<MODE> st = load_cell_state<MODE>(a, a_slot(a, q));  // issued before the walk
             const int r = rep_of_cell(a.grids, a.nrep, q);
             const GridDev& g = a.grids[r];
