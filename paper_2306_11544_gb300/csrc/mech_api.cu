@@ -1433,7 +1433,7 @@ int mech_info(mech_t* h, mech_info_t* out) {
         for (int d = 0; d < 3; ++d) out->dims[d] = h->grids[0].n[d];
     out->voxel = voxel_of(h);
     out->step = h->step;
-    out->launches_per_step = h->n > 0 ? ((h->mode != kFP64 && h->use_tiles) ? 10 : 8) : 0;
+    out->launches_per_step = h->n > 0 ? ((h->mode != kFP64 && h->use_tiles) ? 8 : 6) : 0;
     out->graph_steps = h->graph_steps;
     out->device_bytes = (int64_t)h->dev_bytes;
     return MECH_OK;
