@@ -180,10 +180,11 @@ __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float l
         const float gA = fmaf(S2, A2m1, fmaf(eS, A2m1, g));
         const float ta = __fdividef(gA, AS * (AS + d));
         float cf = -(aij * (sccai * sccaj)) * (ta * ta);
-        if (d < S) {
-            const float t = __fdividef(g, S * (S + d));
-            cf += (sccri * sccrj) * (t * t);
-        }
+        // repulsion for d < S, as a select: the lanes of a warp's hit loop
+        // then run one path (S (S + d) > 0, so the unused quotient is finite)
+        const float t = __fdividef(g, S * (S + d));
+        const float cr = cf + (sccri * sccrj) * (t * t);
+        cf = d < S ? cr : cf;
         const float sc = cf * rd;
         f = make_float3(sc * rx, sc * ry, sc * rz);
         return true;
