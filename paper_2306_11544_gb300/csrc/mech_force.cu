@@ -154,6 +154,23 @@ struct Acc3 {
 //   ulp even where d/S is close to 1, which a direct 1 - d/S is not.  The
 //   adhesion term uses (A S)^2 - d^2 = S^2 (A^2 - 1) + (S^2 - d^2), A2m1 being
 //   A^2 - 1 rounded once.
+// Approximate FP32 reciprocal square root and quotient in their PTX forms
+// that flush subnormal operands and results to zero (no scaling path for
+// them): d^2 > 0 is checked first and S (S + d) is of the order of R^2, so
+// no operand of the pair term is subnormal, and a subnormal quotient would
+// stand for a term below 1e-38.  For normal values the results equal those
+// of rsqrtf and __fdividef.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float div_ftz(float a, float b) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
                                            float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
                                            float aij, float A, float A2m1, float3& f) {
@@ -171,18 +188,18 @@ __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float l
         const float D = two_sum(D1, pz, e2);
         const float De = ((fmaf(hx, hx, -px) + fmaf(hy, hy, -py)) + (fmaf(hz, hz, -pz) + (e1 + e2))) +
                          (lx * (2.f * hx + lx) + ly * (2.f * hy + ly) + lz * (2.f * hz + lz));
-        const float rd = rsqrtf(d2);
+        const float rd = rsqrt_ftz(d2);
         const float d = d2 * rd;
         // g = S^2 - d^2, with S^2 = S2 + eS; then (A S)^2 - d^2 = S^2 (A^2 - 1) + g
         const float S2 = S * S;
         const float eS = fmaf(S, S, -S2) + 2.f * S * Se;
         const float g = (S2 - D) + (eS - De);
         const float gA = fmaf(S2, A2m1, fmaf(eS, A2m1, g));
-        const float ta = __fdividef(gA, AS * (AS + d));
+        const float ta = div_ftz(gA, AS * (AS + d));
         float cf = -(aij * (sccai * sccaj)) * (ta * ta);
         // repulsion for d < S, as a select: the lanes of a warp's hit loop
         // then run one path (S (S + d) > 0, so the unused quotient is finite)
-        const float t = __fdividef(g, S * (S + d));
+        const float t = div_ftz(g, S * (S + d));
         const float cr = cf + (sccri * sccrj) * (t * t);
         cf = d < S ? cr : cf;
         const float sc = cf * rd;
