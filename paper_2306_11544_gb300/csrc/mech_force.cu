@@ -1049,12 +1049,23 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                 for (uint32_t t = s_vox_toff[v]; t < s_vox_toff[v + 1]; ++t) s_tvox[t] = (uint8_t)v;
         }
         __syncthreads();
-        // 4. one thread per target
+        // 4. one thread per target; in a warp pass with g <= 16 targets (the
+        // last pass of a tile) each target's candidate list is split into L
+        // contiguous parts (L lanes per target, L g <= 32) whose Kahan sums
+        // are combined by a fixed tree, so the pass costs a fraction of a
+        // full one instead of the work of its busiest target
         const uint32_t T = s_vox_toff[NVOX];
         for (uint32_t t0 = (uint32_t)warp * 32u; t0 < T; t0 += kTT) {
-            const uint32_t t = t0 + lane;
-            const bool valid = t < T;
-            uint32_t nkey = 0, ntile = 0, q = 0;
+            const uint32_t gcnt = min(32u, T - t0);
+            const uint32_t lsh = gcnt > 16u ? 0u : gcnt > 8u ? 1u : gcnt > 4u ? 2u : gcnt > 2u ? 3u : gcnt > 1u ? 4u : 5u;
+            const uint32_t L = 1u << lsh;
+            const uint32_t part = lane & (L - 1u);
+            const uint32_t t = t0 + (lane >> lsh);
+            const bool valid = (lane >> lsh) < gcnt;
+            uint32_t nkey = 0, ntile = 0, q = 0, src = 0;
+            float Ri = 0.f, Rlo_i = 0.f;
+            Acc3 acc;
+            acc.zero();
             if (valid) {
                 const int v = s_tvox[t];
                 const uint32_t k = t - s_vox_toff[v];
@@ -1062,22 +1073,23 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                 const int rr = (cy + 1) + HY * (cz + 1);
                 const uint32_t in_row = s_row_vb[rr][cx + 1] + k;
                 q = s_row_gs[rr] + in_row;
-                const uint32_t src = a_slot(a, q);  // its state, read after the scan
+                if (part == 0u) src = a_slot(a, q);  // its state, read after the scan
                 const uint32_t si = s_row_off[rr] + in_row;
                 const float4 pi = srec[2 * si];
                 const float4 qi = srec[2 * si + 1];
                 const float4 li = record_lo(pi, qi, g.qs);
+                Ri = pi.w;
+                Rlo_i = li.w;
                 const float cut_i = fmaf(A, pi.w, g.qm + a.cut_eps);
-                Acc3 acc;
-                acc.zero();
-                // scan the list in blocks of 32 candidates (up to three blocks at a
-                // time): a branch-free test on the hi parts builds one hit mask per
-                // block, then the exact pair terms of all hits (from hi + lo) are
-                // summed in list order in a single loop, so a warp's divergent
-                // iterations are its largest total hit count, not a sum of
-                // per-block maxima
-                const uint32_t l0 = s_vox_loff[v], l1 = s_vox_loff[v + 1];
-                for (uint32_t cb = l0; cb < l1; cb += 96u) {
+                // this lane's part [p0, p1) of the voxel's list, scanned in blocks
+                // of 32 candidates (up to three blocks at a time): a branch-free
+                // test on the hi parts builds one hit mask per block, then the
+                // exact pair terms of all hits (from hi + lo) are summed in list
+                // order in a single loop, so a warp's divergent iterations are
+                // its largest total hit count, not a sum of per-block maxima
+                const uint32_t l0 = s_vox_loff[v], len = s_vox_loff[v + 1] - l0;
+                const uint32_t p0 = l0 + ((len * part) >> lsh), l1 = l0 + ((len * (part + 1u)) >> lsh);
+                for (uint32_t cb = p0; cb < l1; cb += 96u) {
                     uint32_t m[3] = {0u, 0u, 0u};
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
@@ -1116,11 +1128,28 @@ __global__ void __launch_bounds__(TileCfg<LX, LZ>::TT, TileCfg<LX, LZ>::MINB) k_
                     else
                         hits(std::false_type{});
                 }
+            }
+            // the parts of a target: lane part + o's sum into lane part, for
+            // part a multiple of 2 o (all lanes take part in the shuffles)
+            for (uint32_t o = 1u; o < L; o <<= 1) {
+                const float ox = __shfl_down_sync(0xFFFFFFFFu, acc.x, o);
+                const float oy = __shfl_down_sync(0xFFFFFFFFu, acc.y, o);
+                const float oz = __shfl_down_sync(0xFFFFFFFFu, acc.z, o);
+                const float ocx = __shfl_down_sync(0xFFFFFFFFu, acc.cx, o);
+                const float ocy = __shfl_down_sync(0xFFFFFFFFu, acc.cy, o);
+                const float ocz = __shfl_down_sync(0xFFFFFFFFu, acc.cz, o);
+                if ((part & (2u * o - 1u)) == 0u) {
+                    acc.add(ox, oy, oz);
+                    acc.add(-ocx, -ocy, -ocz);
+                }
+            }
+            const bool owner = valid && part == 0u;
+            if (owner) {
                 int nix, niy, niz;
-                nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), pi.w, li.w, nix, niy, niz);
+                nkey = ab2_epilogue<MODE>(a, g, q, src, acc.vx(), acc.vy(), acc.vz(), Ri, Rlo_i, nix, niy, niz);
                 ntile = tile_index(g, nix, niy, niz, a.ltx, a.lty, a.ltz);
             }
-            next_step_counts(a, q, nkey, ntile, valid);
+            next_step_counts(a, q, nkey, ntile, owner);
         }
     }
 }
