@@ -775,7 +775,8 @@ int create_impl(mech_t** out, int32_t nrep, const int64_t* counts, const double*
 int stage_out(mech_t* h) {
     StepArgs a = h->args(h->cur, 1);
     const StateBuf& s = h->st[h->cur];
-    CUDA_TRY(launch_unpermute_pos(a, s, h->d_io, h->stream));
+    CUDA_TRY(launch_unpermute_pos(a, s, h->d_io, h->d_io + 3 * (size_t)h->npad, h->d_tmp,
+                                 8 * (size_t)h->npad, h->stream));
     if (h->mode == kFP64)
         CUDA_TRY(launch_unpermute_vel(a, s, nullptr, s.vp64, h->d_io + 3 * (size_t)h->npad, h->stream));
     else
@@ -1069,7 +1070,8 @@ int mech_read_positions(mech_t* h, double* out3n) {
     if (h->n == 0) return MECH_OK;
     if (!out3n) return fail(MECH_E_ARG, "null output");
     StepArgs a = h->args(h->cur, 1);
-    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->stream));
+    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->d_io + 3 * (size_t)h->npad, h->d_tmp,
+                                 8 * (size_t)h->npad, h->stream));
     CUDA_TRY(cudaMemcpyAsync(out3n, h->d_io, 3 * (size_t)h->n * 8, cudaMemcpyDeviceToHost, h->stream));
     return mech_sync(h);
 }
@@ -1386,7 +1388,8 @@ int mech_pair_stats(mech_t* h, int64_t* candidates, int64_t* pairs) {
         return fail(MECH_E_STATE, "a device error left the state inconsistent; reload it with mech_load_state");
     // FP64 positions in caller order, then a binning pass into the B buffers
     StepArgs a = h->args(h->cur, 1);
-    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->stream));
+    CUDA_TRY(launch_unpermute_pos(a, h->st[h->cur], h->d_io, h->d_io + 3 * (size_t)h->npad, h->d_tmp,
+                                 8 * (size_t)h->npad, h->stream));
     h->keys_valid = false;
     MECH_TRY(ensure_keys(h));
     CUDA_TRY(launch_scan(a.count_cur, h->Vpad, h->d_bsum, h->d_start, nullptr, h->d_occ, h->stream));

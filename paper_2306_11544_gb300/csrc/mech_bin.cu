@@ -278,21 +278,61 @@ __global__ void k_canon(const StepArgs a) {
     }
 }
 
-// Voxel order -> caller order (positions), through the id of each slot.
-__global__ void k_unpermute_pos(const StepArgs a, const StateBuf st, double* __restrict__ out) {
+// Voxel order -> caller order (positions), in two passes through buckets of
+// 2,048 consecutive caller ids.  Pass 1, in slot order: each cell appends its
+// position to its bucket's run of the staging buffer (a bucket holds exactly
+// its 2,048 ids, so the runs need no counting pass; the order inside a run
+// comes from atomics) and the id's low 11 bits beside it.  Pass 2, one block
+// per bucket: the run is placed by those bits into shared memory and written
+// out contiguously.  (A direct scatter through the ids, three 8-byte writes
+// per cell at random places of the output, measured slower end to end.)
+constexpr uint32_t kUpLog = 11, kUpIds = 1u << kUpLog;
+
+__global__ void k_unpermute_pos_stage(const StepArgs a, const StateBuf st, uint32_t* __restrict__ cursor,
+                                      double* __restrict__ stage, uint16_t* __restrict__ low) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
         const uint32_t id = st.id[q];
+        double x[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double x;
             if (a.mode == kMixedKahan)
-                x = __dsub_rn((double)st.posf[(size_t)d * a.npad + q], (double)st.comp[(size_t)d * a.npad + q]);
+                x[d] = __dsub_rn((double)st.posf[(size_t)d * a.npad + q], (double)st.comp[(size_t)d * a.npad + q]);
             else
-                x = st.pos64[(size_t)d * a.npad + q];
-            out[3 * (size_t)id + d] = x;
+                x[d] = st.pos64[(size_t)d * a.npad + q];
+        }
+        if (id >= a.n) {  // only after an earlier device error
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+        const uint32_t bkt = id >> kUpLog;
+        const uint32_t k = atomicAdd(&cursor[bkt], 1u);
+        const size_t r = ((size_t)bkt << kUpLog) + k;  // k < the bucket's id count (ids are a permutation)
+        if (k >= kUpIds || r >= a.n) {
+            atomicOr(a.err, kErrIndex);
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) stage[3 * r + d] = x[d];
+        low[r] = (uint16_t)(id & (kUpIds - 1u));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_unpermute_pos_place(uint32_t n, const double* __restrict__ stage,
+                                                             const uint16_t* __restrict__ low,
+                                                             double* __restrict__ out) {
+    __shared__ double sh[3 * kUpIds];
+    const size_t base = (size_t)blockIdx.x << kUpLog;
+    const uint32_t cnt = (uint32_t)min((size_t)kUpIds, (size_t)n - base);
+    for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const uint32_t j = low[base + k];
+        if (j < cnt) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sh[3 * j + d] = stage[3 * (base + k) + d];
         }
     }
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < 3 * cnt; w += blockDim.x) out[3 * base + w] = sh[w];
 }
 
 __global__ void k_unpermute_vel(const StepArgs a, const StateBuf st, const float* __restrict__ vf,
@@ -662,9 +702,22 @@ cudaError_t launch_shift(const StepArgs& a, const uint32_t* shift, double* io, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s) {
+size_t unpermute_scratch_bytes(uint32_t n) {
+    const size_t nb = ((size_t)n + kUpIds - 1) >> kUpLog;
+    return ((2 * (size_t)n + 255) / 256) * 256 + 4 * nb;
+}
+
+cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, double* stage, void* scratch,
+                                 size_t scratch_cap, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    k_unpermute_pos<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, out);
+    if (unpermute_scratch_bytes(a.n) > scratch_cap) return cudaErrorInvalidValue;
+    const uint32_t nb = (a.n + kUpIds - 1) >> kUpLog;
+    uint16_t* low = static_cast<uint16_t*>(scratch);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) + ((2 * (size_t)a.n + 255) / 256) * 256);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, 4 * (size_t)nb, s);
+    if (e != cudaSuccess) return e;
+    k_unpermute_pos_stage<<<elementwise_grid(a.n), 256, 0, s>>>(a, st, cursor, stage, low);
+    k_unpermute_pos_place<<<nb, 256, 0, s>>>(a.n, stage, low, out);
     return cudaGetLastError();
 }
 

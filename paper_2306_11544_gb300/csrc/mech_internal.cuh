@@ -244,7 +244,13 @@ cudaError_t launch_scan_blocks(const uint32_t* count, uint32_t vpad, uint32_t* b
                                uint32_t* start, uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
 cudaError_t launch_scatter(const StepArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_canon(const StepArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, cudaStream_t s);
+// Positions in caller order (3n doubles into out); stage: 3n doubles of
+// device scratch; scratch: scratch_cap bytes (256-aligned) of device scratch,
+// at least unpermute_scratch_bytes(n), about 2n (cudaErrorInvalidValue
+// otherwise).
+size_t unpermute_scratch_bytes(uint32_t n);
+cudaError_t launch_unpermute_pos(const StepArgs& a, const StateBuf& st, double* out, double* stage, void* scratch,
+                                 size_t scratch_cap, cudaStream_t s);
 
 // ---- dynamic population, between steps (mech_api.cu: mech_remove_cells /
 // mech_add_cells) ----
