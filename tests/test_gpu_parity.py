@@ -285,6 +285,39 @@ def test_tiled_force_matches_oracle(mode, tiling, kernel):
         check_bins(m, pop, mode)
 
 
+@pytest.mark.parametrize("mode", ["mixed", "kahan"])
+def test_tile_passes_of_few_targets_split_lists(mode):
+    """Interior tiles holding 1 to 40 cells: a warp pass of the block-per-tile
+    kernel with g <= 16 targets splits each target's candidate list over
+    32 / g lanes (2 to 32) and combines the parts' Kahan sums by a tree of
+    shuffles; with 17 to 32 targets it is one lane per target, and 33 or
+    more take a second pass.  Every count is present, each cluster packed
+    tightly enough that most cells interact, and the velocities match the
+    oracle."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    h = 30.0
+    counts = [1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 40]
+    xyz = []
+    k = 0
+    for bz in range(1, 4):
+        for by in range(1, 4):
+            for bx in range(1, 3):
+                if k == len(counts):
+                    break
+                c = (np.array([bx, by, bz]) * 4 + 2) * h  # centre of the tile
+                xyz.append(c + rng.uniform(-20.0, 20.0, size=(counts[k], 3)))
+                k += 1
+    xyz = np.concatenate(xyz)
+    pop = H.tiny_population(xyz, [0.0] * 3, [4 * 5 * h] * 3, h=h)
+    with H.make(pop, mode) as m:
+        m.set_dense_kernel("block_per_tile")
+        m.set_tiling((4, 4, 4), 1)
+        v = m.compute_velocities()
+    vref = oracle.velocities(xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, H.dims_of(pop))
+    assert np.abs(vref).max() > 1.0  # the clusters interact
+    assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+
+
 @pytest.mark.parametrize("kernel", DENSE_KERNELS)
 @pytest.mark.parametrize("tile", [(4, 4, 4), (4, 4, 8), (8, 4, 4)])
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
