@@ -308,6 +308,14 @@ int build_grids(mech_t* h) {
         G.inv_q = (float)std::ldexp(1.0, k);
         G.qs = (float)std::ldexp(1.0, -k - 15);
         G.qm = 2.0f * G.q;
+        G.qexp = -k;
+        G.qf24 = (float)std::ldexp(1.0, -k - 24);
+        G.fix_ok = 1;
+        for (int d = 0; d < 3; ++d) {
+            const double f = std::ldexp(G.oc[d], k + 24);
+            if (!(std::fabs(f) < std::ldexp(1.0, 61))) G.fix_ok = 0;
+            G.oc_fix[d] = G.fix_ok ? std::llround(f) : 0;
+        }
         G.tbase = (uint32_t)tsum;
         tsum += (uint64_t)G.nt[0] * (uint64_t)G.nt[1] * (uint64_t)G.nt[2];
         if (vsum > (uint64_t)0x7FFFFFFF - 2 * (uint64_t)kScanTile)

@@ -258,6 +258,7 @@ __global__ void k_canon(const StepArgs a) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double x = xd[d];
+                if (g.fix_ok && split_fixed(x, g, d, hi[d], lo[d])) continue;
                 const double rr = __dsub_rn(x, g.oc[d]);
                 const double t = rint(__dmul_rn(rr, (double)g.inv_q));
                 if (fabs(t) < 8388608.0) {

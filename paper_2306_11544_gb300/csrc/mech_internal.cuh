@@ -97,6 +97,13 @@ struct GridDev {
     float q, inv_q;    // grid of the hi parts (a power of two)
     float qs;          // q / 2^15: unit of the 16-bit position residuals
     float qm;          // candidate-test margin (>= 2 q)
+    // The centre in fixed point, units of q / 2^24 (oc_fix = round(oc 2^24 / q)),
+    // for an FP64 position's split into hi + lo with integer arithmetic;
+    // fix_ok = 0 where a coordinate's fixed-point value could reach 2^61.
+    long long oc_fix[3];
+    int32_t qexp;      // q = 2^qexp
+    int32_t fix_ok;
+    float qf24;        // q / 2^24
 };
 
 // Position relative to the grid centre -> hi on the q grid (|hi| < 2^23 q);
@@ -105,6 +112,36 @@ struct GridDev {
 __device__ __forceinline__ float quantize_hi(float r, float q, float inv_q) {
     const float t = r * inv_q;
     return fabsf(t) < 8388608.f ? rintf(t) * q : r;
+}
+
+// FP64 position x -> hi + lo relative to the grid centre, without FP64
+// arithmetic (this GPU's FP64 pipe runs at 1/64 of the FP32 rate): x is
+// rounded to a multiple of q / 2^24 as a 64-bit integer X (from its exponent
+// and mantissa), D = X - oc_fix, hi = round(D / 2^24) q (exact, |hi| < 2^23 q)
+// and lo = (D - 2^24 round(D / 2^24)) q / 2^24 (exact: |lo| <= q / 2).  The
+// error against x - oc is at most q / 2^24, far below the 16-bit residual
+// stored in the record (q / 2^15).  Returns false (the caller then takes the
+// FP64 route) for a non-finite x, |X| >= 2^62, or |hi| >= 2^23 q.
+__device__ __forceinline__ bool split_fixed(double x, const GridDev& g, int d, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FFull);
+    if (E == 0x7FF) return false;
+    long long X = 0;
+    if (E != 0) {  // (a subnormal x counts as 0)
+        const long long M = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53 bits
+        const int sh = E - 1075 - g.qexp + 24;  // x / (q 2^-24) = M 2^sh
+        if (sh > 8) return false;
+        if (sh >= 0) X = M << sh;
+        else if (sh > -63) X = (M + (1ll << (-sh - 1))) >> (-sh);  // to nearest, ties up
+        if (b >> 63) X = -X;
+    }
+    const long long D = X - g.oc_fix[d];
+    const long long H = (D + (1ll << 23)) >> 24;  // nearest multiple of 2^24 (ties up)
+    if (H >= (1ll << 23) || H <= -(1ll << 23)) return false;
+    const int L = (int)(D - H * (1ll << 24));  // in [-2^23, 2^23)
+    hi = (float)(int)H * g.q;
+    lo = (float)L * g.qf24;
+    return true;
 }
 
 // 16-bit fixed point with offset 2^15: v in [-1, 1) units -> [0, 65535].
