@@ -401,7 +401,7 @@ int ensure_keys(mech_t* h) {
         CUDA_TRY(launch_zero_u32(h->d_bcount[p], h->Vpad / kScanTile, h->stream));
         CUDA_TRY(launch_zero_u32(h->d_tcount[p], h->NT, h->stream));
     }
-    CUDA_TRY(launch_keys(a, h->elem_grid, h->stream));
+    CUDA_TRY(launch_keys(a, h->elem_grid, h->Vpad, h->stream));
     h->keys_valid = true;
     return MECH_OK;
 }

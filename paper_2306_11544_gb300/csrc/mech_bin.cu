@@ -41,7 +41,6 @@ __global__ void k_keys(const StepArgs a) {
             tile = tile_index(g, ix, iy, iz, a.ltx, a.lty, a.ltz);
         }
         warp_add(a.count_cur, key, valid);
-        warp_add(a.bcount_cur, key / (uint32_t)kScanTile, valid);
         warp_add(a.tcount_cur, tile, valid);
         if (valid) a.key[i] = key;
     }
@@ -297,10 +296,12 @@ __global__ void k_unpermute_pos_stage(const StepArgs a, const StateBuf st, uint3
         double x[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if (a.mode == kMixedKahan)
-                x[d] = __dsub_rn((double)st.posf[(size_t)d * a.npad + q], (double)st.comp[(size_t)d * a.npad + q]);
-            else
+            if (a.mode == kMixedKahan) {
+                const float xh = st.posf[(size_t)d * a.npad + q], c = st.comp[(size_t)d * a.npad + q];
+                if (!join_f32_double(xh, c, x[d])) x[d] = __dsub_rn((double)xh, (double)c);
+            } else {
                 x[d] = st.pos64[(size_t)d * a.npad + q];
+            }
         }
         if (id >= a.n) {  // only after an earlier device error
             atomicOr(a.err, kErrIndex);
@@ -363,7 +364,7 @@ __global__ void k_load_pos(const StepArgs a, const StateBuf st, const double* __
                 if (raw_kahan) {
                     xh = (float)x;
                     c = comp_in ? (float)comp_in[3 * (size_t)id + d] : 0.0f;
-                } else {
+                } else if (!split_double_f32(x, xh, c)) {
                     xh = __double2float_rn(x);
                     c = __double2float_rn(__dsub_rn((double)xh, x));
                 }
@@ -618,9 +619,12 @@ cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s) {
-    if (a.n == 0) return cudaSuccess;
-    k_keys<<<grid, 256, 0, s>>>(a);
+cudaError_t launch_keys(const StepArgs& a, int grid, uint32_t vpad, cudaStream_t s) {
+    if (a.n != 0) k_keys<<<grid, 256, 0, s>>>(a);
+    // the scan's block sums of this histogram, by the reduce pass (per-warp
+    // atomics into them from the key pass contend: consecutive warps of the
+    // voxel-sorted cells hit the same 8,192-voxel block)
+    k_scan_reduce<<<vpad / kScanTile, kScanThreads, 0, s>>>(a.count_cur, a.bcount_cur);
     return cudaGetLastError();
 }
 

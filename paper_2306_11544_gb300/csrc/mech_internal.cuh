@@ -144,6 +144,86 @@ __device__ __forceinline__ bool split_fixed(double x, const GridDev& g, int d, f
     return true;
 }
 
+// FP64 <-> compensated FP32 pair without FP64 arithmetic (this GPU's FP64
+// pipe runs at 1/64 of the FP32 rate; these run where positions cross the
+// host boundary).  Both give bit for bit the IEEE results of the FP64 forms
+// they replace, and return false (the caller then takes the FP64 form) where
+// that would need more care: zero, subnormal or non-finite operands, a float
+// overflow, or a scale outside the normal range.
+//
+// x -> (xh, c) with xh = RN_f32(x) and c = RN_f32(xh - x): the 53-bit
+// significand S of x is rounded to 24 bits (ties to even); r = S24 2^29 - S
+// is then xh - x in units of 2^(E - 1075), a 30-bit integer, and c is its
+// float conversion (one rounding) times that power of two (exact).
+__device__ __forceinline__ bool split_double_f32(double x, float& xh, float& c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FFull);
+    if (E < 949 || E == 0x7FF) return false;  // |x| < 2^-74, or not finite
+    const long long S = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    long long S24 = S >> 29;
+    const long long R = S & 0x1FFFFFFFll;
+    if (R > 0x10000000ll || (R == 0x10000000ll && (S24 & 1))) ++S24;
+    const int r = (int)((S24 << 29) - S);  // |r| <= 2^28
+    int ef = E - 1023;
+    long long S24m = S24;
+    if (S24 == (1ll << 24)) {
+        S24m = 1ll << 23;
+        ++ef;
+    }
+    if (ef > 127) return false;
+    const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+    xh = __uint_as_float(sgn | ((unsigned int)(ef + 127) << 23) | (unsigned int)(S24m - (1ll << 23)));
+    if (r == 0) {
+        c = 0.0f;
+    } else {
+        const float scale = __uint_as_float((unsigned int)(E - 1075 + 127) << 23);  // 2^(E - 1075)
+        c = __uint_as_float(__float_as_uint(__int2float_rn(r) * scale) ^ sgn);
+    }
+    return true;
+}
+
+// (xh, c) -> (double)xh - (double)c, rounded to nearest (ties to even): both
+// are 24-bit significands S1 2^k1, S2 2^k2; for 0 <= k1 - k2 <= 39 the exact
+// difference is a 64-bit integer times 2^k2, normalised and rounded here.
+__device__ __forceinline__ bool join_f32_double(float xh, float c, double& x) {
+    const unsigned int b1 = __float_as_uint(xh), b2 = __float_as_uint(c);
+    const int E1 = (int)((b1 >> 23) & 0xFFu);
+    if (E1 == 0 || E1 == 0xFF) return false;
+    const long long S1 = (long long)((b1 & 0x7FFFFFu) | 0x800000u);
+    const unsigned long long s1 = (unsigned long long)(b1 >> 31);
+    if ((b2 & 0x7FFFFFFFu) == 0u) {  // c = 0: x = xh exactly
+        x = __longlong_as_double(
+            (long long)((s1 << 63) | ((unsigned long long)(E1 + 896) << 52) | ((unsigned long long)(S1 - (1ll << 23)) << 29)));
+        return true;
+    }
+    const int E2 = (int)((b2 >> 23) & 0xFFu);
+    if (E2 == 0 || E2 == 0xFF) return false;
+    const int g = E1 - E2;
+    if (g < 0 || g > 39) return false;
+    const long long S2 = (long long)((b2 & 0x7FFFFFu) | 0x800000u);
+    const long long X = ((b1 >> 31) ? -S1 : S1) * (1ll << g) - ((b2 >> 31) ? -S2 : S2);
+    if (X == 0) {
+        x = 0.0;
+        return true;
+    }
+    const unsigned long long sg = X < 0 ? 1ull : 0ull;
+    unsigned long long U = (unsigned long long)(X < 0 ? -X : X);
+    const int lz = __clzll((long long)U);
+    U <<= lz;
+    const unsigned long long rnd = U & 0x7FFull;
+    unsigned long long mant = (U >> 11) & 0xFFFFFFFFFFFFFull;
+    long long ex = 1023 + 63 - lz + (E2 - 150);
+    if (rnd > 0x400ull || (rnd == 0x400ull && (mant & 1ull))) {
+        if (++mant == (1ull << 52)) {
+            mant = 0;
+            ++ex;
+        }
+    }
+    if (ex <= 0 || ex >= 0x7FF) return false;
+    x = __longlong_as_double((long long)((sg << 63) | ((unsigned long long)ex << 52) | mant));
+    return true;
+}
+
 // 16-bit fixed point with offset 2^15: v in [-1, 1) units -> [0, 65535].
 __device__ __forceinline__ uint32_t fix16(float v_units) {
     const float t = fminf(fmaxf(rintf(v_units * 32768.f), -32768.f), 32767.f);
@@ -271,7 +351,9 @@ int device_sms();
 
 // ---- launch wrappers (mech_bin.cu) ----
 cudaError_t launch_zero_u32(uint32_t* p, size_t count, cudaStream_t s);
-cudaError_t launch_keys(const StepArgs& a, int grid, cudaStream_t s);
+// Keys and histograms of the cells in A order, and the histogram's scan-block
+// sums (bcount_cur) for the step's scan.
+cudaError_t launch_keys(const StepArgs& a, int grid, uint32_t vpad, cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* count, uint32_t vpad, uint32_t* bsum, uint32_t* start,
                         uint32_t* zero_word, uint32_t* occ, cudaStream_t s);
 // The same scan when bsum already holds the cells of each block of kScanTile
