@@ -412,9 +412,9 @@ int enqueue_step(mech_t* h, int integrate, bool profile = false) {
     cudaEvent_t* ev = nullptr;
     if (profile && h->prof_steps < mech::kProfCap) ev = &h->prof_ev[(size_t)h->prof_steps * (mech::kProfPhases + 1)];
     if (ev) CUDA_TRY(cudaEventRecord(ev[0], h->stream));
-    // the scan starts from the block sums counted with the histogram (by the
-    // previous step's force epilogue, or by k_keys) and clears the next
-    // step's block sums
+    // the scan starts from the histogram's block sums (counted by the previous
+    // step's force epilogue, or summed by the reduce pass after k_keys) and
+    // clears the next step's block sums
     CUDA_TRY(launch_scan_blocks(a.count_cur, h->Vpad, a.bcount_cur, a.bcount_nxt, h->d_start, h->d_ndense,
                                 h->d_occ, h->stream));
     if (ev) CUDA_TRY(cudaEventRecord(ev[1], h->stream));

@@ -144,16 +144,6 @@ struct Acc3 {
     __device__ __forceinline__ float vz() const { return __fsub_rn(z, cz); }
 };
 
-// Pair term (FP32) for a candidate at offset r = x_i - x_j, given as an exact
-// hi part h (a difference of values on the q grid) plus a small lo part l;
-// Rlo is the sum of the two radius residuals R - (float)R.  Sets f to
-// (c_r - c_a) r / d and returns true if 0 < d < A S (else f = 0, false).
-//   1 - d/S is formed as (S^2 - d^2) / (S (S + d)), with d^2 and S^2 carried
-//   as unevaluated sums (error-free products and sums), so the cancellation of
-//   1 - d/S near contact costs no accuracy: t and t_a are accurate to a few
-//   ulp even where d/S is close to 1, which a direct 1 - d/S is not.  The
-//   adhesion term uses (A S)^2 - d^2 = S^2 (A^2 - 1) + (S^2 - d^2), A2m1 being
-//   A^2 - 1 rounded once.
 // Approximate FP32 reciprocal square root and quotient in their PTX forms
 // that flush subnormal operands and results to zero (no scaling path for
 // them): d^2 > 0 is checked first and S (S + d) is of the order of R^2, so
@@ -171,6 +161,16 @@ __device__ __forceinline__ float div_ftz(float a, float b) {
     return r;
 }
 
+// Pair term (FP32) for a candidate at offset r = x_i - x_j, given as an exact
+// hi part h (a difference of values on the q grid) plus a small lo part l;
+// Rlo is the sum of the two radius residuals R - (float)R.  Sets f to
+// (c_r - c_a) r / d and returns true if 0 < d < A S (else f = 0, false).
+//   1 - d/S is formed as (S^2 - d^2) / (S (S + d)), with d^2 and S^2 carried
+//   as unevaluated sums (error-free products and sums), so the cancellation of
+//   1 - d/S near contact costs no accuracy: t and t_a are accurate to a few
+//   ulp even where d/S is close to 1, which a direct 1 - d/S is not.  The
+//   adhesion term uses (A S)^2 - d^2 = S^2 (A^2 - 1) + (S^2 - d^2), A2m1 being
+//   A^2 - 1 rounded once.
 __device__ __forceinline__ bool pair_force(float hx, float hy, float hz, float lx, float ly, float lz, float Ri,
                                            float Rj, float Rlo, float sccri, float sccai, float sccrj, float sccaj,
                                            float aij, float A, float A2m1, float3& f) {
