@@ -34,8 +34,8 @@
 //   pipe runs at about 1/60 of its FP32 rate, and it, not memory, bounds the
 //   solver), IEEE operations in a fixed order, so every value is
 //   reproducible run to run.  Gradients: central differences inside,
-//   one-sided at the faces, zero along an axis of one voxel; array
-//   [s][axis][v].
+//   one-sided at the faces, zero along an axis of one voxel, each difference
+//   times the reciprocal of dx or 2 dx; array [s][axis][v].
 //
 // GB300 mapping: the work is a set of independent recurrences (one per end
 // of a grid line), so every kernel runs two threads per line.  Lines along y
@@ -337,26 +337,30 @@ __global__ void k_diff_yz(double* __restrict__ rho, int axis, int32_t S, int64_t
                         });
 }
 
-__global__ void k_diff_gradient(const double* __restrict__ rho, int32_t S, int64_t nx, int64_t ny, int64_t nz,
-                                double dx, double* __restrict__ grad) {
-    const int64_t nv = nx * ny * nz;
-    const int64_t total = (int64_t)S * nv;
-    const double two_dx = __dmul_rn(2.0, dx);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = t / nv, v = t - s * nv;
-        const int64_t x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
-        const double* r = rho + s * nv;
-        const int64_t n[3] = {nx, ny, nz};
-        const int64_t i[3] = {x, y, z};
-        const int64_t st[3] = {1, nx, nx * ny};
+// Gradients, one thread per (substrate, voxel) value: differences divided
+// by dx or 2 dx as products with their reciprocals (formed once on the host:
+// an FP64 division costs about six FP64 additions here), and 32-bit index
+// arithmetic (at most 4e9 values per handle).
+__global__ void k_diff_gradient(const double* __restrict__ rho, int32_t S, uint32_t nx, uint32_t ny, uint32_t nz,
+                                double inv_dx, double inv_2dx, double* __restrict__ grad) {
+    const uint32_t nxy = nx * ny, nv = nxy * nz;
+    const uint32_t total = (uint32_t)S * nv;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const uint32_t s = t / nv, v = t - s * nv;
+        const uint32_t z = v / nxy, rem = v - z * nxy;
+        const uint32_t y = rem / nx, x = rem - y * nx;
+        const double* r = rho + (size_t)s * nv;
+        const uint32_t n[3] = {nx, ny, nz};
+        const uint32_t i[3] = {x, y, z};
+        const uint32_t st[3] = {1u, nx, nxy};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             double g;
-            if (n[a] == 1) g = 0.0;
-            else if (i[a] == 0) g = __ddiv_rn(__dsub_rn(r[v + st[a]], r[v]), dx);
-            else if (i[a] == n[a] - 1) g = __ddiv_rn(__dsub_rn(r[v], r[v - st[a]]), dx);
-            else g = __ddiv_rn(__dsub_rn(r[v + st[a]], r[v - st[a]]), two_dx);
-            grad[(s * 3 + a) * nv + v] = g;
+            if (n[a] == 1u) g = 0.0;
+            else if (i[a] == 0u) g = __dmul_rn(__dsub_rn(r[v + st[a]], r[v]), inv_dx);
+            else if (i[a] == n[a] - 1u) g = __dmul_rn(__dsub_rn(r[v], r[v - st[a]]), inv_dx);
+            else g = __dmul_rn(__dsub_rn(r[v + st[a]], r[v - st[a]]), inv_2dx);
+            grad[((size_t)s * 3 + a) * nv + v] = g;
         }
     }
 }
@@ -559,8 +563,8 @@ int mech_diffusion_step(mech_diffusion_t* h, double dt, int64_t n_steps) {
 
 int mech_diffusion_gradient(mech_diffusion_t* h, double* grad) {
     DTRY(dcheck(h));
-    k_diff_gradient<<<grid_for((int64_t)h->S * h->nv, 256, h->sms), 256, 0, h->stream>>>(h->d_rho, h->S, h->nx, h->ny,
-                                                                                        h->nz, h->dx, h->d_grad);
+    k_diff_gradient<<<grid_for((int64_t)h->S * h->nv, 256, h->sms), 256, 0, h->stream>>>(
+        h->d_rho, h->S, (uint32_t)h->nx, (uint32_t)h->ny, (uint32_t)h->nz, 1.0 / h->dx, 0.5 / h->dx, h->d_grad);
     DTRY(dcuda(cudaGetLastError(), "gradient"));
     if (grad)
         DTRY(dcuda(cudaMemcpyAsync(grad, h->d_grad, (size_t)3 * h->nv * h->S * 8, cudaMemcpyDeviceToHost,

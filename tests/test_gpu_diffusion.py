@@ -14,7 +14,9 @@ a difference does not grow along the line: a solve differs by a few u of
 max |rho|, and a step (three solves) by about 10 u.  The tests take
 8 u per solve, i.e. 24 u = 2.7e-15 per step, relative to max |rho|, times the
 number of steps; gradients are differences of two densities divided by dx
-(or 2 dx), so they differ by at most 2 / dx times the density bound."""
+(or 2 dx; the kernels multiply by the reciprocal), so they differ by at
+most 2 / dx times the density bound plus a rounding of the quotient (2 ulp
+of max |rho| / dx, a twelfth of that bound after one step)."""
 import numpy as np
 import pytest
 
