@@ -141,6 +141,30 @@ def force_traffic():
         return None
 
 
+def issue_roofline(tr, args, n, t_tiles):
+    """The tile kernel against the instruction-issue ceiling that binds it:
+    its warp instructions per launch (ncu, from the committed summary of the
+    same source, scaled by the cell count) over its CUDA-event time, against
+    SMs x 4 schedulers x the maximum SM clock.  Only for the configuration
+    the count was taken on."""
+    tk = (tr or {}).get("tile_kernel")
+    if not tk or args.workload != "clustered_20m" or args.mode != "kahan" or args.tile != "4,4,4" \
+            or args.dense_min != 12 or args.dense_kernel != "block_per_tile" or t_tiles <= 0:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    try:
+        with open(PEAKS_FILE) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        mhz = 2070.0
+    instr = tk["warp_instructions_per_launch"] * n / tk["cells"]
+    peak = sms * 4 * mhz * 1e6
+    return {"unit": "warp instructions/s", "achieved": instr / t_tiles, "peak": peak,
+            "frac": instr / t_tiles / peak, "instructions_per_launch": instr,
+            "source": tk["source"]}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
 
@@ -841,6 +865,9 @@ def main():
                 "work": {"neighbour_tests_performed": cand_done, "neighbour_tests_on_workload_grid": cand,
                          "interacting_pairs": pairs},
                 "note": "not bound by HBM: instruction issue (ncu: profiles/force_tile_clustered_20m_x0.25.md)"}
+        issue = issue_roofline(tr, args, n, phases["tiles"] / psteps * 1e-3)
+        if issue:
+            roof["issue"] = issue
     # algorithmic model on the workload's own voxel grid (the internal grid the
     # autotuner may pick is a performance choice, not work of the problem)
     reps = [wl] if not batched else wl.reps
