@@ -169,6 +169,35 @@ def test_checkpoint_resume_is_bitwise(mode):
         assert np.array_equal(resumed[k], full[k]), k
 
 
+@pytest.mark.parametrize("offset", [0.0, 1.0e6, 3.0e7])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "kahan"])
+def test_domains_far_from_the_origin(mode, offset):
+    """The 2k spheroid and its domain translated far from the origin: the
+    record build's integer split of FP64 positions (and, at 3e7 um, its
+    fallback to FP64 arithmetic, whose fixed-point centre would pass 2^61),
+    and the integer conversions between FP64 and the compensated FP32 pair
+    at large exponents, over three steps against the oracle (FP64 mode bit
+    for bit; the FP32 modes at the mixed tolerance, relative to the largest
+    velocity)."""
+    base = synth.spheroid_2k(seed=5)
+    shift = np.array([offset, -0.5 * offset, 0.25 * offset])
+    pop = synth.Population("far", base.xyz + shift, base.R, base.ccr, base.cca, base.ctype, base.lo + shift,
+                           base.hi + shift, A=base.A, h=base.h, dt=base.dt, steps=3)
+    dims = H.dims_of(pop)
+    xr, _, _ = oracle.run(pop.xyz, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, dims, pop.dt, 3)
+    with H.make(pop, mode) as m:
+        m.step(3)
+        x = m.positions()
+        v = m.compute_velocities()
+    vref = oracle.velocities(xr, pop.R, pop.ccr, pop.cca, pop.A, pop.lo, pop.h, dims)
+    if mode == "fp64":
+        assert np.array_equal(x, xr)
+        assert np.array_equal(v, vref)
+    else:
+        assert np.abs(x - xr).max() <= H.TOL_X_MIXED
+        assert H.rel_err(v, vref) <= H.TOL_V_MIXED
+
+
 @pytest.mark.parametrize("mode", ["mixed", "kahan"])
 def test_internal_voxel_keeps_the_pair_set(mode):
     """A finer internal voxel (>= 2 A max R) changes only the FP32 order."""
