@@ -198,7 +198,9 @@ inline int regs_for(int64_t n) { return n <= 2 * kRegsSmall + 1 ? kRegsSmall : (
 // thread (line l = tid mod 32, end = tid / 32) solves one end of line l, the
 // ends meet through shared memory, and the block writes the lines back.  The
 // shared row stride is odd (in doubles), so the 16 lanes of a half-warp hit
-// 16 different banks.
+// 16 different banks.  MAXC > 0: a line end (at most MAXC values) is solved
+// in registers; the launch bound caps registers so that six blocks fit on
+// an SM (the 75^3 grid's 704 blocks then run in one wave).
 template <int MAXC>
 __global__ void __launch_bounds__(2 * kLineTile, 6) k_diff_x_tiled(double* __restrict__ rho, int64_t lines, int64_t nx,
                                                                int64_t ny, int64_t nz, int64_t nmax,
