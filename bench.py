@@ -141,28 +141,30 @@ def force_traffic():
         return None
 
 
-def issue_roofline(tr, args, n, t_tiles):
+def issue_roofline(tr, args, n, t_tiles, sms, mhz):
     """The tile kernel against the instruction-issue ceiling that binds it:
     its warp instructions per launch (ncu, from the committed summary of the
-    same source, scaled by the cell count) over its CUDA-event time, against
-    SMs x 4 schedulers x the maximum SM clock.  Only for the configuration
-    the count was taken on."""
+    same source, scaled by the cell count) over its CUDA-event time t_tiles
+    (s), against sms SMs x 4 schedulers x mhz.  Only for the configuration
+    the count was taken on; None otherwise."""
     tk = (tr or {}).get("tile_kernel")
     if not tk or args.workload != "clustered_20m" or args.mode != "kahan" or args.tile != "4,4,4" \
             or args.dense_min != 12 or args.dense_kernel != "block_per_tile" or t_tiles <= 0:
         return None
-    import torch
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    try:
-        with open(PEAKS_FILE) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
-    except Exception:
-        mhz = 2070.0
     instr = tk["warp_instructions_per_launch"] * n / tk["cells"]
     peak = sms * 4 * mhz * 1e6
     return {"unit": "warp instructions/s", "achieved": instr / t_tiles, "peak": peak,
             "frac": instr / t_tiles / peak, "instructions_per_launch": instr,
             "source": tk["source"]}
+
+
+def sm_max_mhz():
+    """Maximum SM clock from the generated peaks file (2,070 MHz if absent)."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 2070.0
 
 
 class ClockSampler:
@@ -865,7 +867,8 @@ def main():
                 "work": {"neighbour_tests_performed": cand_done, "neighbour_tests_on_workload_grid": cand,
                          "interacting_pairs": pairs},
                 "note": "not bound by HBM: instruction issue (ncu: profiles/force_tile_clustered_20m_x0.25.md)"}
-        issue = issue_roofline(tr, args, n, phases["tiles"] / psteps * 1e-3)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        issue = issue_roofline(tr, args, n, phases["tiles"] / psteps * 1e-3, sms, sm_max_mhz())
         if issue:
             roof["issue"] = issue
     # algorithmic model on the workload's own voxel grid (the internal grid the

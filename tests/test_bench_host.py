@@ -53,3 +53,23 @@ def test_replicate_sharding_covers_every_replicate_once_and_balances():
         assert shard.shard_replicates(counts, world) == parts  # deterministic
     with pytest.raises(ValueError):
         shard.shard_replicates([5, 6], 3)
+
+
+def test_issue_roofline_only_for_the_counted_configuration():
+    """The bench line's issue roofline scales the committed instruction count
+    by the cell count and divides by the kernel time and SMs x 4 schedulers x
+    clock; for any other configuration than the one counted it is absent."""
+    import argparse
+    tr = {"tile_kernel": {"warp_instructions_per_launch": 1000, "cells": 10, "source": "test"}}
+    args = argparse.Namespace(workload="clustered_20m", mode="kahan", tile="4,4,4", dense_min=12,
+                              dense_kernel="block_per_tile")
+    r = bench.issue_roofline(tr, args, 20, 2e-3, 10, 1000.0)
+    assert r["instructions_per_launch"] == 2000
+    assert r["achieved"] == pytest.approx(1e6) and r["peak"] == pytest.approx(4e10)
+    assert r["frac"] == pytest.approx(2.5e-5)
+    for change in ({"mode": "mixed"}, {"tile": "4,4,8"}, {"dense_min": 16}, {"workload": "spheroid_1m"},
+                   {"dense_kernel": "warp_per_voxel"}):
+        other = argparse.Namespace(**{**vars(args), **change})
+        assert bench.issue_roofline(tr, other, 20, 2e-3, 10, 1000.0) is None
+    assert bench.issue_roofline(None, args, 20, 2e-3, 10, 1000.0) is None
+    assert bench.issue_roofline({}, args, 20, 2e-3, 10, 1000.0) is None
